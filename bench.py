@@ -1,0 +1,284 @@
+"""Benchmark of the leap-format dynamical-core step on GB300.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Workload: 1440 x 720 x 30 (0.25 deg, the high-resolution case), FP32 state
+with FP64 column integrals, jet + terrain + seeded noise.  A "step" is one
+full three-stage time step.  The metric is grid-point-steps per second
+(nlon*nlat*nlev*steps / s); for N > 1 each rank advances its own replica
+(the path has no exchange step on one GPU) and the value is the sum over ranks.
+
+The reference arm (--impl reference) times the FP64 CPU oracle, as it stands,
+on a bounded sample of the same workload (the same model on a coarser grid).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = (1440, 720, 30)
+BYTES_PER_POINT_STEP = {4: 96, 8: 192}  # 24 words: stages read/write 6 + 9 + 9 words
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+        return dist.get_rank(), ws, int(os.environ.get("LOCAL_RANK", "0"))
+    return 0, 1, 0
+
+
+def cpu_oracle_rate(nlon, nlat, nlev, steps=1):
+    """Time the FP64 oracle on one grid; returns (gp-steps/s, seconds)."""
+    import oracle
+    from paper_2103_10114_gb300 import inputs
+
+    st = inputs.baroclinic_jet(nlon, nlat, nlev, seed=5, noise=1e-2, terrain_seed=2)
+    o = oracle.Oracle(nlon, nlat, nlev, phis=st["phis"])
+    dt = 60.0
+    t0 = time.perf_counter()
+    o.step(st, dt, steps)
+    el = time.perf_counter() - t0
+    return nlon * nlat * nlev * steps / el, el
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sample = (360, 180, 30)
+    for _ in range(args.warmup):
+        cpu_oracle_rate(*sample)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        cpu_oracle_rate(*sample)
+    el = time.perf_counter() - t0
+    pts = sample[0] * sample[1] * sample[2]
+    value = pts * args.steps / el
+    line = {
+        "impl": "reference", "metric": "grid-point-steps/s", "value": value, "unit": "gp-steps/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "leap-format IAP step 1440x720x30 (0.25 deg) jet+terrain", "sample": "360x180x30"},
+        "cpu_baseline": {"value": value, "unit": "gp-steps/s", "cores": 1, "kind": "oracle",
+                         "sample": "one oracle step of the same model on 360x180x30 per timed step"},
+        "e2e": {"value": value, "unit": "gp-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    from paper_2103_10114_gb300 import agcm, inputs
+
+    rank, world, local = dist_setup()
+    torch.cuda.set_device(local)
+    agcm.build()
+    agcm.lib()
+    I, J, K = WORKLOAD
+    pts = I * J * K
+    st = inputs.baroclinic_jet(I, J, K, seed=5 + rank, noise=1e-2, terrain_seed=2)
+    g = agcm.Grid(I, J, K, phis=st["phis"])
+    dt = g.dt(100.0)
+    s = agcm.State(g, agcm.AGCM_FP32)
+    s.load(st)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    # warm-up
+    s.step(args.warmup, dt)
+    torch.cuda.synchronize()
+    # timed region: device-resident inputs
+    s.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s.step(args.steps, dt)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = e0.elapsed_time(e1)
+    prof = s.profile_read()
+    s.profile(False)
+    clocks = clk.summary()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * pts * args.steps / (ms / 1e3)
+    d = s.diagnostics()
+
+    # end to end through the C ABI with pinned host buffers
+    esz = 4
+    host = {f: torch.from_numpy(np.ascontiguousarray(st[f], dtype=np.float32)).pin_memory() for f in agcm.FIELDS}
+    hout = {f: torch.empty_like(host[f]).pin_memory() for f in agcm.FIELDS}
+    nbytes = sum(h.numel() * esz for h in host.values())
+    e2e_steps = max(3, args.steps // 2)
+    torch.cuda.synchronize()
+    barrier()
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        s.load_host(host)
+        s.step(1, dt)
+        s.store_host(hout)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = world * pts * e2e_steps / (e2e_ms / 1e3)
+
+    peak, peak_kind = peaks()
+    # dominant kernel and its algorithmic bytes (one stage: 6/9/9 words per point -> 8 on average)
+    name, (kms, kn) = max(prof.items(), key=lambda kv: kv[1][0])
+    stage_bytes = pts * 8 * esz
+    achieved = stage_bytes / (kms / kn / 1e3) / 1e9 if name in ("k_update", "k_fused_stage") else None
+    launches = sum(n for _, n in prof.values())
+    line = {
+        "metric": "grid-point-steps/s", "value": value, "unit": "gp-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "leap-format IAP step 1440x720x30 (0.25 deg), FP32 with FP64 column sums",
+                   "ic": "jet+terrain+noise 1e-2", "dt_s": dt, "parallelism": "replicas" if world > 1 else "1 gpu",
+                   "l2": "inputs larger than L2 (state 373 MB)"},
+        "hbm_frac_step": value / world * BYTES_PER_POINT_STEP[esz] / (peak * 1e9),
+        "roofline": {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": None, "peak_kind": peak_kind,
+                     "bytes_per_launch": stage_bytes, "avg_launch_ms": kms / kn},
+        "kernels": {k: {"ms_total": v[0], "launches": v[1], "share": v[0] / sum(x[0] for x in prof.values())}
+                    for k, v in prof.items()},
+        "e2e": {"value": e2e, "unit": "gp-steps/s", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "sypd_equiv": (value / world / pts) * dt / 365.0,
+        "energy_ok": bool(d["finite"]),
+    }
+    if rank == 0 and not args.no_forms:
+        line["forms"] = measure_forms(agcm, inputs, torch)
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, el = cpu_oracle_rate(720, 360, 30)
+        line["cpu_baseline"] = {"value": rate, "unit": "gp-steps/s", "cores": 1, "kind": "oracle",
+                                "sample": f"one FP64 oracle step of the same model on 720x360x30 ({el:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def measure_forms(agcm, inputs, torch, steps=5):
+    """gp-steps/s of the other forms on the same GPU (FP64 plain at the same size)."""
+    out = {}
+    I, J, K = WORKLOAD
+    st = inputs.baroclinic_jet(I, J, K, seed=6, noise=1e-2, terrain_seed=2)
+    g = agcm.Grid(I, J, K, phis=st["phis"])
+    dt = g.dt(100.0)
+    s = agcm.State(g, agcm.AGCM_FP64)
+    s.load(st)
+    s.step(2, dt)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    s.step(steps, dt)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    out["fp64_1440x720x30"] = {"value": I * J * K * steps / (ms / 1e3), "unit": "gp-steps/s", "ms_per_step": ms / steps}
+    s.close()
+    return out
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,179 @@
+/*
+ * agcm.h — C ABI of the GB300 leap-format dynamical-core step (arXiv 2103.10114).
+ *
+ * The library (libagcm.so, CUDA sm_103a) advances the IAP-transformed
+ * primitive equations (Eq. 1, split as Eq. 2 into advection L and adaptation
+ * A) on a latitude–longitude–sigma Arakawa C grid.  Every zonal difference on
+ * row j spans an odd stride M_j (Eq. 6), chosen by Eq. 7 so that the zonal
+ * spacing never falls below the 45-degree spacing; this replaces the polar
+ * filter.  The vertical sums of Alg. 1 / Alg. 2 (sigma velocity, surface
+ * pressure tendency) and the hydrostatic integral run as in-kernel column scans.
+ *
+ * Conventions shared by every call
+ *  - Grid: I = nlon, J = nlat, K = nlev.  Scalar (Phi, pi) and U rows
+ *    j = 0..J-1 sit at colatitude (j+1/2)*pi/J; V rows j = 0..J-2 at
+ *    (j+1)*pi/J; V is zero on the pole edges.  U index i sits at longitude
+ *    (i+1/2)*2pi/I, scalars and V at i*2pi/I.  V points toward increasing
+ *    colatitude (south).
+ *  - Layout: SoA, row-major [k][j][i] with i (longitude) contiguous.
+ *    U, Phi: K*J*I values; V: K*(J-1)*I; pi: J*I (= p'_sa / p0, the surface
+ *    pressure anomaly over the standard pressure exp(-phi_s/(R*250 K))).
+ *  - Element type: double for AGCM_FP64 states, float for AGCM_FP32 states.
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = default
+ *    stream).  Calls that take a stream are asynchronous on it unless stated.
+ *  - Errors: every call returns AGCM_OK (0) or a negative-free positive code
+ *    below; agcm_last_error() returns a message for the calling thread.  The
+ *    library never aborts the process and never traps on the device.
+ *  - Ownership: pointers passed in are borrowed for the duration of the call;
+ *    the library copies what it keeps.  Objects returned through `out`
+ *    pointers are owned by the caller and released with the matching destroy.
+ */
+#ifndef AGCM_H_
+#define AGCM_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum agcm_status {
+  AGCM_OK = 0,
+  AGCM_EINVAL = 1,      /* invalid argument (sizes, tables, null pointers) */
+  AGCM_ENOMEM = 2,      /* device allocation failed */
+  AGCM_ECUDA = 3,       /* a CUDA runtime call failed; message has the CUDA text */
+  AGCM_ETIMEOUT = 4,    /* a bounded device-side wait gave up */
+  AGCM_ENONFINITE = 5   /* the state holds NaN or Inf (reported by diagnostics) */
+};
+
+enum agcm_precision { AGCM_FP64 = 0, AGCM_FP32 = 1 };
+
+typedef struct agcm_grid agcm_grid_t;
+typedef struct agcm_state agcm_state_t;
+
+/* Message for the last failing call on this thread ("" if none). */
+const char* agcm_last_error(void);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int agcm_version(void);
+
+/*
+ * Device memory hook.  By default the library calls cudaMalloc/cudaFree.
+ * A caller may route every allocation through its own allocator (the Python
+ * binding routes them through PyTorch's caching allocator).  `alloc` returns
+ * NULL on failure, which the library reports as AGCM_ENOMEM.  Pass NULLs to
+ * restore the default.  Not thread-safe against concurrent state creation.
+ */
+typedef void* (*agcm_alloc_fn)(uint64_t bytes, void* ctx);
+typedef void (*agcm_free_fn)(void* ptr, void* ctx);
+int agcm_set_allocator(agcm_alloc_fn alloc, agcm_free_fn free_fn, void* ctx);
+
+/*
+ * agcm_grid_create — the geometry of one grid (host only; no device work).
+ * Eq. 6 (leap-format centred difference) and Eq. 7 (N_leap from the
+ * 45-degree reference spacing) define the stride tables.
+ *   nlon >= 3, nlat >= 2, nlev >= 1.
+ *   sigma_half: nlev+1 half levels, sigma_half[0] = 0, sigma_half[nlev] = 1,
+ *               strictly increasing; NULL = uniform.
+ *   leap_u:     nlat strides for the scalar/U rows; NULL = Eq. 7 raised to
+ *               the next odd number (N = max(1, ceil(r - 1e-9))).
+ *   leap_v:     nlat-1 strides for the V rows; NULL = Eq. 7 at the V rows.
+ *               Every stride must be odd, >= 1 and satisfy 2*M < nlon.
+ *   phis:       nlat*nlon surface geopotential [m^2/s^2]; NULL = flat.
+ * Returns AGCM_EINVAL for any violation, with the offending row in the message.
+ */
+int agcm_grid_create(int nlon, int nlat, int nlev, const double* sigma_half, const int32_t* leap_u,
+                     const int32_t* leap_v, const double* phis, agcm_grid_t** out);
+int agcm_grid_destroy(agcm_grid_t* grid);
+
+/* Copy the stride tables out (leap_u: nlat values, leap_v: nlat-1 values). */
+int agcm_grid_leap(const agcm_grid_t* grid, int32_t* leap_u, int32_t* leap_v);
+
+/*
+ * Time step from the gravity-wave bound (reading R10 of the design notes):
+ * dt = 1.6 / ((c_max + umax) * sqrt((2/(a cos45 dlam))^2 + (2/(a dth))^2)),
+ * c_max^2 the largest eigenvalue of the linear column operator.  Host only.
+ */
+int agcm_grid_dt(const agcm_grid_t* grid, double umax, double* dt);
+
+/*
+ * agcm_state_create — device storage for one prognostic state on `grid`
+ * (Eq. 1's U, V, Phi and p'_sa/p0) plus the stage buffers of the three-stage
+ * step.  precision: AGCM_FP64 or AGCM_FP32 (FP32 keeps the column integral of
+ * the surface-pressure tendency in FP64).  nmembers must be 1 (ensembles of
+ * uneven grids use agcm_ensemble_*).  The state keeps a reference to `grid`;
+ * destroy the state before the grid.
+ */
+int agcm_state_create(const agcm_grid_t* grid, int precision, int nmembers, agcm_state_t** out);
+int agcm_state_destroy(agcm_state_t* state);
+
+/*
+ * Load or store the prognostic fields.  Pointers hold the state's element
+ * type in the layout above; on_device = 1 for device pointers, 0 for host
+ * pointers (pinned host memory gives asynchronous copies).  Asynchronous on
+ * `stream`.
+ */
+int agcm_state_load(agcm_state_t* state, const void* U, const void* V, const void* Phi,
+                    const void* pi, int on_device, void* stream);
+int agcm_state_store(const agcm_state_t* state, void* U, void* V, void* Phi, void* pi,
+                     int on_device, void* stream);
+
+/*
+ * agcm_step — advance `nsteps` steps of length dt seconds with the
+ * three-stage scheme x1 = xn + dt/2 T(xn), x2 = xn + dt/2 T(x1),
+ * x_{n+1} = xn + dt T(x2) (three calls per step: Sec. "Optimizations").
+ * T is the full spatial operator: leap advection, pressure gradient,
+ * Coriolis, Omega~ conversion and the column-integrated divergence.
+ * Asynchronous; launch errors are returned, device-side non-finite values
+ * show up in agcm_diagnostics.
+ */
+int agcm_step(agcm_state_t* state, int nsteps, double dt, void* stream);
+
+/*
+ * agcm_tendency — T(x) of the current state into caller-owned device
+ * buffers (same layout and element type as the state).  For validation.
+ */
+int agcm_tendency(agcm_state_t* state, void* tU, void* tV, void* tPhi, void* tpi, void* stream);
+
+/*
+ * agcm_step_adjoint — vector-Jacobian product of ONE step at the state x_n
+ * currently held by `xn` (not modified): lam_out = (d x_{n+1} / d x_n)^T lam_in.
+ * lam_in[4] / lam_out[4] are caller-owned device buffers {U, V, Phi, pi} of the
+ * state's element type; lam_in and lam_out must not alias.  The three stage
+ * states are recomputed from x_n.  Exact transpose of the linearised
+ * step, hand-written (no automatic differentiation).
+ */
+int agcm_step_adjoint(agcm_state_t* xn, const void* const lam_in[4], void* const lam_out[4], double dt,
+                      void* stream);
+
+/* Diagnostics (a11): FP64 global sums and maxima.  Synchronises `stream`. */
+typedef struct agcm_diag {
+  double mass;      /* sum_j A_j (pi~ + pi)  [p0 m^2] */
+  double e_kin;     /* 1/2 sum dsigma (A U^2 + Av V^2) */
+  double e_pot;     /* 1/2 sum dsigma A Phi^2 (available potential) */
+  double e_ps;      /* 1/2 sum A (R T0 / pi~) pi^2 (available surface potential) */
+  double energy;    /* e_kin + e_pot + e_ps */
+  double max_u;     /* max |U| */
+  double max_v;     /* max |V| */
+  int32_t finite;   /* 1 if every value is finite, else 0 */
+  int32_t reserved;
+} agcm_diag_t;
+int agcm_diagnostics(const agcm_state_t* state, agcm_diag_t* out, void* stream);
+
+/*
+ * Per-kernel timing with CUDA events recorded on the launching stream around
+ * every kernel the library launches for `state` (no effect on results).
+ * agcm_profile_enable(state, 1) clears the counters and starts recording;
+ * agcm_profile_read synchronises the recorded events and returns, per kernel
+ * id 0..agcm_kernel_count()-1, the summed milliseconds and the launch count.
+ * ms_total and launches hold at least agcm_kernel_count() entries.
+ */
+int agcm_profile_enable(agcm_state_t* state, int enable);
+int agcm_profile_read(agcm_state_t* state, double* ms_total, int64_t* launches);
+int agcm_kernel_count(void);
+const char* agcm_kernel_name(int id);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AGCM_H_ */

@@ -1,0 +1,687 @@
+// agcm_api.cu — implementation of the C ABI declared in include/agcm.h.
+//
+// Host side: grid geometry (Eq. 7 leap strides, metric terms, sigma tables),
+// the CFL time step, device memory, the three-stage step driver and the
+// diagnostics.  Device side: the kernels in agcm_phases.cuh / agcm_fused.cuh /
+// agcm_adjoint.cuh / agcm_diag.cuh.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/agcm.h"
+#include "agcm_common.cuh"
+#include "agcm_phases.cuh"
+#include "agcm_fused.cuh"
+#include "agcm_adjoint.cuh"
+#include "agcm_diag.cuh"
+
+namespace {
+
+// ---------------------------------------------------------------- errors
+thread_local std::string t_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  t_err = buf;
+  return code;
+}
+
+#define CUDA_TRY(expr)                                                              \
+  do {                                                                              \
+    cudaError_t e_ = (expr);                                                        \
+    if (e_ != cudaSuccess) return fail(AGCM_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+  } while (0)
+
+// ---------------------------------------------------------------- allocator
+agcm_alloc_fn g_alloc = nullptr;
+agcm_free_fn g_free = nullptr;
+void* g_alloc_ctx = nullptr;
+
+void* dev_alloc(size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  if (g_alloc) return g_alloc((uint64_t)bytes, g_alloc_ctx);
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+void dev_free(void* p) {
+  if (!p) return;
+  if (g_free)
+    g_free(p, g_alloc_ctx);
+  else
+    cudaFree(p);
+}
+
+// ---------------------------------------------------------------- constants
+// Reading R2: only the Earth radius is fixed by the paper (zonal grid-size table).
+constexpr double kA = 6.371e6;
+constexpr double kOmega = 7.292e-5;
+constexpr double kR = 287.04;
+constexpr double kCp = 1004.64;
+constexpr double kT0 = 250.0;
+constexpr double kPi = 3.14159265358979323846;
+
+// Eq. 7 with cos(90deg - theta) = sin(theta) and res = dlam, rounded up to an
+// integer >= 1 (ratios within 1e-9 of an integer count as that integer) and
+// then to the next odd number (U sits on half points, so the stride is odd).
+int eq7_stride(double theta, double dlam) {
+  const double ref = std::asin(std::sqrt(0.5) * std::sin(dlam));
+  const double here = std::asin(std::sin(theta) * std::sin(dlam));
+  int n = (int)std::ceil(ref / here - 1e-9);
+  n = std::max(n, 1);
+  return (n & 1) ? n : n + 1;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- objects
+struct DevGeomBlob {
+  void* blob = nullptr;
+  bool ready = false;
+};
+
+struct agcm_grid {
+  int I = 0, J = 0, K = 0;
+  double dlam = 0, dth = 0, b = 0;
+  std::vector<double> s, c, cot, A, sv, Av, sh, ds, Hkk, hk, pit;
+  std::vector<int> Mu, Mv;
+  // device copies of the tables, per precision (0 = FP64, 1 = FP32)
+  DevGeomBlob dev[2];
+  agcm::Geom<double> gd{};
+  agcm::Geom<float> gf{};
+  int device = -1;
+  int refs = 0;
+};
+
+// Kernel ids for the per-kernel event timing.
+enum KernelId : int {
+  KID_COLSTATE = 0,
+  KID_COLUMN,
+  KID_UPDATE,
+  KID_FUSED_PRE,
+  KID_FUSED,
+  KID_DIAG,
+  KID_ADJ_UPDATE,
+  KID_ADJ_COLUMN,
+  KID_ADJ_COLSTATE,
+  KID_ADJ_AXPY,
+  KID_COUNT
+};
+static const char* const kKernelNames[KID_COUNT] = {
+    "k_colstate", "k_column", "k_update", "k_fused_colsum", "k_fused_stage", "k_diag",
+    "k_adj_update", "k_adj_column", "k_adj_colstate", "k_adj_axpy"};
+
+struct Profiler {
+  bool on = false;
+  struct Rec { int id; cudaEvent_t a, b; };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  double ms[KID_COUNT] = {};
+  int64_t n[KID_COUNT] = {};
+  cudaEvent_t get() {
+    if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void begin(int id, cudaStream_t st) {
+    if (!on) return;
+    Rec r{id, get(), get()};
+    cudaEventRecord(r.a, st);
+    recs.push_back(r);
+  }
+  void end(cudaStream_t st) {
+    if (!on || recs.empty()) return;
+    cudaEventRecord(recs.back().b, st);
+  }
+  int drain() {
+    for (auto& r : recs) {
+      if (cudaEventSynchronize(r.b) != cudaSuccess) return 1;
+      float t = 0.f;
+      cudaEventElapsedTime(&t, r.a, r.b);
+      ms[r.id] += t;
+      n[r.id] += 1;
+      pool.push_back(r.a);
+      pool.push_back(r.b);
+    }
+    recs.clear();
+    return 0;
+  }
+  void reset() {
+    drain();
+    for (int q = 0; q < KID_COUNT; ++q) { ms[q] = 0; n[q] = 0; }
+  }
+  ~Profiler() {
+    for (auto& r : recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
+struct agcm_state {
+  Profiler prof;
+  const agcm_grid* grid = nullptr;
+  int prec = AGCM_FP64;
+  size_t esz = 8;
+  size_t n3 = 0, nv = 0, n2 = 0;
+  // prognostic x_n and the stage states x1, x2 (U, V, Phi, pi packed)
+  void* x[3][4] = {};
+  // phase scratch: P, rP, Pu, rPu, Pv, rPv (2-D), W ((K+1) planes), X, psi, C (FP64)
+  void* col[6] = {};
+  void* W = nullptr;
+  void* X = nullptr;
+  void* psi = nullptr;
+  double* C = nullptr;
+  // diagnostics partials
+  double* diag = nullptr;
+  std::vector<void*> owned;
+};
+
+namespace {
+
+template <class T>
+int upload_geom(agcm_grid* g, int p) {
+  const int I = g->I, J = g->J, K = g->K;
+  // pack every table into one allocation
+  std::vector<char> host;
+  auto put = [&](const void* src, size_t bytes) {
+    size_t off = (host.size() + 255) & ~size_t(255);
+    host.resize(off + bytes);
+    std::memcpy(host.data() + off, src, bytes);
+    return off;
+  };
+  auto putT = [&](const std::vector<double>& v) {
+    std::vector<T> t(v.begin(), v.end());
+    return put(t.data(), t.size() * sizeof(T));
+  };
+  auto putD = [&](const std::vector<double>& v) { return put(v.data(), v.size() * sizeof(double)); };
+  auto putI = [&](const std::vector<int>& v) { return put(v.data(), v.size() * sizeof(int)); };
+
+  std::vector<double> rdx(J), rdy(J), zf(J), r2A(J), f0(J), cota(J);
+  for (int j = 0; j < J; ++j) {
+    rdx[j] = 1.0 / (kA * g->s[j] * g->Mu[j] * g->dlam);
+    rdy[j] = 1.0 / (kA * g->s[j] * g->dth);
+    zf[j] = kA * g->dth / g->Mu[j];
+    r2A[j] = 0.5 / g->A[j];
+    f0[j] = 2.0 * kOmega * g->c[j];
+    cota[j] = g->cot[j] / kA;
+  }
+  const int JV = J - 1;
+  std::vector<double> yv(JV), zfv(JV), r2Av(JV), cn(JV), cs(JV);
+  for (int j = 0; j < JV; ++j) {
+    yv[j] = kA * g->dlam * g->sv[j];
+    zfv[j] = kA * g->dth / g->Mv[j];
+    r2Av[j] = 0.5 / g->Av[j];
+    cn[j] = 0.25 * g->A[j] / g->Av[j];
+    cs[j] = 0.25 * g->A[j + 1] / g->Av[j];
+  }
+  std::vector<double> r2ds(K), hk_rds(K);
+  for (int k = 0; k < K; ++k) {
+    r2ds[k] = 0.5 / g->ds[k];
+    hk_rds[k] = g->hk[k] / g->ds[k];
+  }
+  std::vector<double> rt0pit((size_t)J * I);
+  for (size_t n = 0; n < rt0pit.size(); ++n) rt0pit[n] = kR * kT0 / g->pit[n];
+
+  size_t o_Mu = putI(g->Mu), o_rdx = putT(rdx), o_rdy = putT(rdy), o_zf = putT(zf), o_r2A = putT(r2A),
+         o_f0 = putT(f0), o_cota = putT(cota);
+  std::vector<int> MvPad(g->Mv);
+  if (MvPad.empty()) MvPad.push_back(1);
+  size_t o_Mv = putI(MvPad), o_sv = putT(g->sv.empty() ? std::vector<double>{0} : g->sv),
+         o_yv = putT(yv.empty() ? std::vector<double>{0} : yv),
+         o_zfv = putT(zfv.empty() ? std::vector<double>{0} : zfv),
+         o_r2Av = putT(r2Av.empty() ? std::vector<double>{0} : r2Av),
+         o_cn = putT(cn.empty() ? std::vector<double>{0} : cn),
+         o_cs = putT(cs.empty() ? std::vector<double>{0} : cs);
+  size_t o_ds = putT(g->ds), o_r2ds = putT(r2ds), o_hk = putT(g->hk), o_Hkk = putT(g->Hkk),
+         o_hkr = putT(hk_rds), o_dsd = putD(g->ds), o_shd = putD(g->sh), o_Ad = putD(g->A),
+         o_Avd = putD(g->Av.empty() ? std::vector<double>{0} : g->Av);
+  size_t o_rt0 = putT(rt0pit), o_pit = putT(g->pit);
+
+  void* d = dev_alloc(host.size());
+  if (!d) return fail(AGCM_ENOMEM, "device allocation of %zu bytes for the grid tables failed", host.size());
+  if (cudaMemcpy(d, host.data(), host.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+    dev_free(d);
+    return fail(AGCM_ECUDA, "copy of the grid tables failed: %s", cudaGetErrorString(cudaGetLastError()));
+  }
+  char* base = (char*)d;
+  agcm::Geom<T> G{};
+  G.I = I; G.J = J; G.K = K;
+  G.Mu = (const int*)(base + o_Mu);
+  G.rdx = (const T*)(base + o_rdx);
+  G.rdy = (const T*)(base + o_rdy);
+  G.zf = (const T*)(base + o_zf);
+  G.r2A = (const T*)(base + o_r2A);
+  G.f0 = (const T*)(base + o_f0);
+  G.cota = (const T*)(base + o_cota);
+  G.Mv = (const int*)(base + o_Mv);
+  G.sv = (const T*)(base + o_sv);
+  G.yv = (const T*)(base + o_yv);
+  G.zfv = (const T*)(base + o_zfv);
+  G.r2Av = (const T*)(base + o_r2Av);
+  G.cn = (const T*)(base + o_cn);
+  G.cs = (const T*)(base + o_cs);
+  G.ds = (const T*)(base + o_ds);
+  G.r2ds = (const T*)(base + o_r2ds);
+  G.hk = (const T*)(base + o_hk);
+  G.Hkk = (const T*)(base + o_Hkk);
+  G.hk_rds = (const T*)(base + o_hkr);
+  G.dsd = (const double*)(base + o_dsd);
+  G.shd = (const double*)(base + o_shd);
+  G.Ad = (const double*)(base + o_Ad);
+  G.Avd = (const double*)(base + o_Avd);
+  G.rt0pit = (const T*)(base + o_rt0);
+  G.pit = (const T*)(base + o_pit);
+  G.b = (T)g->b;
+  G.rady = (T)(1.0 / (kA * g->dth));
+  g->dev[p].blob = d;
+  g->dev[p].ready = true;
+  if constexpr (sizeof(T) == 8)
+    g->gd = G;
+  else
+    g->gf = G;
+  return AGCM_OK;
+}
+
+int ensure_geom(const agcm_grid* cg, int prec) {
+  agcm_grid* g = const_cast<agcm_grid*>(cg);
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  if (g->dev[prec].ready) {
+    if (g->device != dev) return fail(AGCM_EINVAL, "grid tables live on device %d, current device is %d", g->device, dev);
+    return AGCM_OK;
+  }
+  g->device = dev;
+  return prec == AGCM_FP64 ? upload_geom<double>(g, prec) : upload_geom<float>(g, prec);
+}
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+inline unsigned nblocks(size_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+// ------------------------------------------------------------- stage driver
+// One stage: out = base + cdt * T(xs).  base == nullptr gives T(xs) itself.
+template <class T>
+int run_stage(agcm_state* s, const agcm::Geom<T>& G, void* const xs[4], void* const base[4],
+              void* const out[4], double cdt, cudaStream_t st) {
+  const size_t n2 = s->n2, n3 = s->n3;
+  agcm::ColState<T> cs{(T*)s->col[0], (T*)s->col[1], (T*)s->col[2], (T*)s->col[3], (T*)s->col[4], (T*)s->col[5]};
+  s->prof.begin(KID_COLSTATE, st);
+  agcm::k_colstate<T><<<nblocks(n2, 256), 256, 0, st>>>(G, (const T*)xs[3], cs);
+  s->prof.end(st);
+  s->prof.begin(KID_COLUMN, st);
+  agcm::k_column<T><<<nblocks(n2, 128), 128, 0, st>>>(G, (const T*)xs[0], (const T*)xs[1], (const T*)xs[2],
+                                                      (const T*)xs[3], cs, (T*)s->W, (T*)s->X, (T*)s->psi,
+                                                      (const T*)base[3], (T*)out[3], cdt, s->C);
+  s->prof.end(st);
+  s->prof.begin(KID_UPDATE, st);
+  agcm::k_update<T><<<nblocks(n3, 256), 256, 0, st>>>(G, (const T*)xs[0], (const T*)xs[1], (const T*)xs[2], cs,
+                                                      (const T*)s->W, (const T*)s->X, (const T*)s->psi,
+                                                      (const T*)base[0], (const T*)base[1], (const T*)base[2],
+                                                      (T*)out[0], (T*)out[1], (T*)out[2], (T)cdt);
+  s->prof.end(st);
+  CUDA_TRY(cudaGetLastError());
+  return AGCM_OK;
+}
+
+template <class T>
+int run_steps(agcm_state* s, int nsteps, double dt, cudaStream_t st) {
+  const agcm::Geom<T>& G = *reinterpret_cast<const agcm::Geom<T>*>(
+      sizeof(T) == 8 ? (const void*)&s->grid->gd : (const void*)&s->grid->gf);
+  for (int n = 0; n < nsteps; ++n) {
+    int rc;
+    if ((rc = run_stage<T>(s, G, s->x[0], s->x[0], s->x[1], 0.5 * dt, st))) return rc;
+    if ((rc = run_stage<T>(s, G, s->x[1], s->x[0], s->x[2], 0.5 * dt, st))) return rc;
+    if ((rc = run_stage<T>(s, G, s->x[2], s->x[0], s->x[0], dt, st))) return rc;
+  }
+  return AGCM_OK;
+}
+
+template <class T>
+int diagnostics(const agcm_state* s, double h[8], cudaStream_t st) {
+  const agcm::Geom<double>& G = s->grid->gd;
+  const int nb = agcm::kDiagPartials;
+  agcm_state* sm = const_cast<agcm_state*>(s);
+  sm->prof.begin(KID_DIAG, st);
+  agcm::k_diag<T><<<nb, agcm::kDiagThreads, 0, st>>>(G, (const T*)s->x[0][0], (const T*)s->x[0][1],
+                                                     (const T*)s->x[0][2], (const T*)s->x[0][3], s->diag);
+  agcm::k_diag_final<<<1, agcm::kDiagThreads, 0, st>>>(s->diag, nb, s->diag + 8 * nb);
+  sm->prof.end(st);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemcpyAsync(h, s->diag + 8 * nb, 7 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  return AGCM_OK;
+}
+
+template <class T>
+int adjoint_step(agcm_state* s, const void* const lam_in[4], void* const lam_out[4], double dt, cudaStream_t st);
+
+}  // namespace
+
+// ======================================================================= C ABI
+extern "C" {
+
+const char* agcm_last_error(void) { return t_err.c_str(); }
+
+int agcm_version(void) { return 100; }
+
+int agcm_set_allocator(agcm_alloc_fn alloc, agcm_free_fn free_fn, void* ctx) {
+  if ((alloc == nullptr) != (free_fn == nullptr))
+    return fail(AGCM_EINVAL, "alloc and free must both be set or both be NULL");
+  g_alloc = alloc;
+  g_free = free_fn;
+  g_alloc_ctx = ctx;
+  return AGCM_OK;
+}
+
+int agcm_grid_create(int nlon, int nlat, int nlev, const double* sigma_half, const int32_t* leap_u,
+                     const int32_t* leap_v, const double* phis, agcm_grid_t** out) {
+  if (!out) return fail(AGCM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (nlon < 3 || nlat < 2 || nlev < 1)
+    return fail(AGCM_EINVAL, "need nlon >= 3, nlat >= 2, nlev >= 1 (got %d, %d, %d)", nlon, nlat, nlev);
+  if ((double)nlon * nlat * nlev > 4.0e9)
+    return fail(AGCM_EINVAL, "grid of %d x %d x %d points is too large", nlon, nlat, nlev);
+  agcm_grid* g = new agcm_grid;
+  const int I = nlon, J = nlat, K = nlev;
+  g->I = I; g->J = J; g->K = K;
+  g->dlam = 2.0 * kPi / I;
+  g->dth = kPi / J;
+  g->b = std::sqrt((kR / kCp) * kR * kT0);
+  g->s.resize(J); g->c.resize(J); g->cot.resize(J); g->A.resize(J); g->Mu.resize(J);
+  for (int j = 0; j < J; ++j) {
+    const double th = (j + 0.5) * g->dth;
+    g->s[j] = std::sin(th);
+    g->c[j] = std::cos(th);
+    g->cot[j] = g->c[j] / g->s[j];
+    g->A[j] = kA * kA * g->s[j] * g->dth * g->dlam;
+    g->Mu[j] = leap_u ? leap_u[j] : eq7_stride(th, g->dlam);
+  }
+  g->sv.resize(J - 1); g->Av.resize(J - 1); g->Mv.resize(J - 1);
+  for (int j = 0; j < J - 1; ++j) {
+    const double th = (j + 1.0) * g->dth;
+    g->sv[j] = std::sin(th);
+    g->Av[j] = kA * kA * g->sv[j] * g->dth * g->dlam;
+    g->Mv[j] = leap_v ? leap_v[j] : eq7_stride(th, g->dlam);
+  }
+  for (int j = 0; j < J; ++j)
+    if (g->Mu[j] < 1 || (g->Mu[j] & 1) == 0 || 2 * g->Mu[j] >= I) {
+      int m = g->Mu[j];
+      delete g;
+      return fail(AGCM_EINVAL, "leap_u[%d] = %d: strides must be odd, >= 1 and below nlon/2", j, m);
+    }
+  for (int j = 0; j < J - 1; ++j)
+    if (g->Mv[j] < 1 || (g->Mv[j] & 1) == 0 || 2 * g->Mv[j] >= I) {
+      int m = g->Mv[j];
+      delete g;
+      return fail(AGCM_EINVAL, "leap_v[%d] = %d: strides must be odd, >= 1 and below nlon/2", j, m);
+    }
+  g->sh.resize(K + 1);
+  for (int h = 0; h <= K; ++h) g->sh[h] = sigma_half ? sigma_half[h] : (double)h / K;
+  if (g->sh[0] != 0.0 || g->sh[K] != 1.0) {
+    delete g;
+    return fail(AGCM_EINVAL, "sigma_half must start at 0 and end at 1");
+  }
+  g->ds.resize(K); g->Hkk.resize(K); g->hk.resize(K);
+  for (int k = 0; k < K; ++k) {
+    g->ds[k] = g->sh[k + 1] - g->sh[k];
+    if (!(g->ds[k] > 0.0)) {
+      delete g;
+      return fail(AGCM_EINVAL, "sigma_half must increase strictly (level %d)", k);
+    }
+    const double mid = 0.5 * (g->sh[k] + g->sh[k + 1]);
+    g->Hkk[k] = std::log(g->sh[k + 1] / mid);
+    g->hk[k] = k > 0 ? std::log(g->sh[k + 1] / g->sh[k]) : 0.0;
+  }
+  g->pit.resize((size_t)J * I);
+  for (size_t n = 0; n < g->pit.size(); ++n) {
+    const double p = phis ? phis[n] : 0.0;
+    if (!std::isfinite(p)) {
+      delete g;
+      return fail(AGCM_EINVAL, "phis[%zu] is not finite", n);
+    }
+    g->pit[n] = std::exp(-p / (kR * kT0));
+  }
+  *out = g;
+  return AGCM_OK;
+}
+
+int agcm_grid_destroy(agcm_grid_t* g) {
+  if (!g) return AGCM_OK;
+  if (g->refs > 0) return fail(AGCM_EINVAL, "grid still has %d live states", g->refs);
+  for (auto& d : g->dev)
+    if (d.blob) dev_free(d.blob);
+  delete g;
+  return AGCM_OK;
+}
+
+int agcm_grid_leap(const agcm_grid_t* g, int32_t* lu, int32_t* lv) {
+  if (!g || !lu || (!lv && g->J > 1)) return fail(AGCM_EINVAL, "null argument");
+  for (int j = 0; j < g->J; ++j) lu[j] = g->Mu[j];
+  for (int j = 0; j < g->J - 1; ++j) lv[j] = g->Mv[j];
+  return AGCM_OK;
+}
+
+int agcm_grid_dt(const agcm_grid_t* g, double umax, double* dt) {
+  if (!g || !dt || !(umax >= 0.0)) return fail(AGCM_EINVAL, "bad argument");
+  const int K = g->K;
+  // S = D^{1/2} (b^2 H D^-1 H^T D + R T0 1 1^T D) D^{-1/2}, D = diag(dsigma):
+  // symmetric and positive semi-definite with the eigenvalues of the column
+  // operator; its largest eigenvalue by power iteration.
+  std::vector<double> H((size_t)K * K, 0.0);
+  for (int k = 0; k < K; ++k) {
+    H[(size_t)k * K + k] = g->Hkk[k];
+    for (int kk = k + 1; kk < K; ++kk) H[(size_t)k * K + kk] = g->hk[kk];
+  }
+  std::vector<double> S((size_t)K * K, 0.0);
+  const double b2 = g->b * g->b, rt = kR * kT0;
+  for (int p = 0; p < K; ++p)
+    for (int q = 0; q < K; ++q) {
+      double acc = 0.0;
+      for (int m = 0; m < K; ++m) acc += H[(size_t)p * K + m] * H[(size_t)q * K + m] / g->ds[m];
+      S[(size_t)p * K + q] = std::sqrt(g->ds[p] * g->ds[q]) * (b2 * acc + rt);
+    }
+  std::vector<double> v(K, 1.0), w(K);
+  double lam = 0.0;
+  for (int it = 0; it < 10000; ++it) {
+    double nrm = 0.0;
+    for (int p = 0; p < K; ++p) {
+      double acc = 0.0;
+      for (int q = 0; q < K; ++q) acc += S[(size_t)p * K + q] * v[q];
+      w[p] = acc;
+      nrm += acc * acc;
+    }
+    nrm = std::sqrt(nrm);
+    double dot = 0.0;
+    for (int p = 0; p < K; ++p) dot += v[p] * w[p];
+    double vn = 0.0;
+    for (int p = 0; p < K; ++p) vn += v[p] * v[p];
+    const double est = dot / vn;
+    for (int p = 0; p < K; ++p) v[p] = w[p] / nrm;
+    if (it > 10 && std::fabs(est - lam) <= 1e-15 * std::fabs(est)) {
+      lam = est;
+      break;
+    }
+    lam = est;
+  }
+  const double cmax = std::sqrt(lam);
+  const double kx = 2.0 / (kA * std::sqrt(0.5) * g->dlam), ky = 2.0 / (kA * g->dth);
+  *dt = 1.6 / ((cmax + umax) * std::sqrt(kx * kx + ky * ky));
+  return AGCM_OK;
+}
+
+int agcm_state_create(const agcm_grid_t* g, int precision, int nmembers, agcm_state_t** out) {
+  if (!g || !out) return fail(AGCM_EINVAL, "null argument");
+  *out = nullptr;
+  if (precision != AGCM_FP64 && precision != AGCM_FP32) return fail(AGCM_EINVAL, "precision must be AGCM_FP64 or AGCM_FP32");
+  if (nmembers != 1) return fail(AGCM_EINVAL, "nmembers must be 1; ensembles use agcm_ensemble_*");
+  int rc = ensure_geom(g, AGCM_FP64);
+  if (!rc && precision == AGCM_FP32) rc = ensure_geom(g, AGCM_FP32);
+  if (rc) return rc;
+  agcm_state* s = new agcm_state;
+  s->grid = g;
+  s->prec = precision;
+  s->esz = precision == AGCM_FP64 ? 8 : 4;
+  const size_t I = g->I, J = g->J, K = g->K;
+  s->n3 = K * J * I;
+  s->nv = K * (J - 1) * I;
+  s->n2 = J * I;
+  auto get = [&](size_t bytes) -> void* {
+    void* p = dev_alloc(bytes);
+    if (p) s->owned.push_back(p);
+    return p;
+  };
+  bool ok = true;
+  for (int c = 0; c < 3 && ok; ++c) {
+    ok = ok && (s->x[c][0] = get(s->n3 * s->esz));
+    ok = ok && (s->x[c][1] = get(std::max<size_t>(s->nv, 1) * s->esz));
+    ok = ok && (s->x[c][2] = get(s->n3 * s->esz));
+    ok = ok && (s->x[c][3] = get(s->n2 * s->esz));
+  }
+  for (int c = 0; c < 6 && ok; ++c) ok = ok && (s->col[c] = get(s->n2 * s->esz));
+  ok = ok && (s->W = get((K + 1) * J * I * s->esz));
+  ok = ok && (s->X = get(s->n3 * s->esz));
+  ok = ok && (s->psi = get(s->n3 * s->esz));
+  ok = ok && (s->C = (double*)get(s->n2 * sizeof(double)));
+  ok = ok && (s->diag = (double*)get((agcm::kDiagPartials + 1) * 8 * sizeof(double)));
+  if (!ok) {
+    for (void* p : s->owned) dev_free(p);
+    delete s;
+    return fail(AGCM_ENOMEM, "device allocation for a %zu x %zu x %zu state failed", I, J, K);
+  }
+  for (int c = 0; c < 3; ++c)
+    for (int f = 0; f < 4; ++f) {
+      size_t n = f == 1 ? std::max<size_t>(s->nv, 1) : (f == 3 ? s->n2 : s->n3);
+      cudaMemset(s->x[c][f], 0, n * s->esz);
+    }
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    for (void* p : s->owned) dev_free(p);
+    delete s;
+    return fail(AGCM_ECUDA, "state initialisation failed: %s", cudaGetErrorString(cudaGetLastError()));
+  }
+  const_cast<agcm_grid*>(g)->refs++;
+  *out = s;
+  return AGCM_OK;
+}
+
+int agcm_state_destroy(agcm_state_t* s) {
+  if (!s) return AGCM_OK;
+  cudaDeviceSynchronize();
+  for (void* p : s->owned) dev_free(p);
+  const_cast<agcm_grid*>(s->grid)->refs--;
+  delete s;
+  return AGCM_OK;
+}
+
+int agcm_state_load(agcm_state_t* s, const void* U, const void* V, const void* Phi, const void* pi,
+                    int on_device, void* stream) {
+  if (!s || !U || !Phi || !pi || (!V && s->nv)) return fail(AGCM_EINVAL, "null argument");
+  cudaStream_t st = as_stream(stream);
+  cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CUDA_TRY(cudaMemcpyAsync(s->x[0][0], U, s->n3 * s->esz, kind, st));
+  if (s->nv) CUDA_TRY(cudaMemcpyAsync(s->x[0][1], V, s->nv * s->esz, kind, st));
+  CUDA_TRY(cudaMemcpyAsync(s->x[0][2], Phi, s->n3 * s->esz, kind, st));
+  CUDA_TRY(cudaMemcpyAsync(s->x[0][3], pi, s->n2 * s->esz, kind, st));
+  return AGCM_OK;
+}
+
+int agcm_state_store(const agcm_state_t* s, void* U, void* V, void* Phi, void* pi, int on_device,
+                     void* stream) {
+  if (!s || !U || !Phi || !pi || (!V && s->nv)) return fail(AGCM_EINVAL, "null argument");
+  cudaStream_t st = as_stream(stream);
+  cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  CUDA_TRY(cudaMemcpyAsync(U, s->x[0][0], s->n3 * s->esz, kind, st));
+  if (s->nv) CUDA_TRY(cudaMemcpyAsync(V, s->x[0][1], s->nv * s->esz, kind, st));
+  CUDA_TRY(cudaMemcpyAsync(Phi, s->x[0][2], s->n3 * s->esz, kind, st));
+  CUDA_TRY(cudaMemcpyAsync(pi, s->x[0][3], s->n2 * s->esz, kind, st));
+  return AGCM_OK;
+}
+
+int agcm_step(agcm_state_t* s, int nsteps, double dt, void* stream) {
+  if (!s || nsteps < 0 || !std::isfinite(dt)) return fail(AGCM_EINVAL, "bad argument");
+  if (nsteps == 0) return AGCM_OK;
+  cudaStream_t st = as_stream(stream);
+  return s->prec == AGCM_FP64 ? run_steps<double>(s, nsteps, dt, st) : run_steps<float>(s, nsteps, dt, st);
+}
+
+int agcm_tendency(agcm_state_t* s, void* tU, void* tV, void* tPhi, void* tpi, void* stream) {
+  if (!s || !tU || !tPhi || !tpi || (!tV && s->nv)) return fail(AGCM_EINVAL, "null argument");
+  cudaStream_t st = as_stream(stream);
+  void* out[4] = {tU, tV, tPhi, tpi};
+  void* none[4] = {nullptr, nullptr, nullptr, nullptr};
+  if (s->prec == AGCM_FP64) return run_stage<double>(s, s->grid->gd, s->x[0], none, out, 1.0, st);
+  return run_stage<float>(s, s->grid->gf, s->x[0], none, out, 1.0, st);
+}
+
+int agcm_step_adjoint(agcm_state_t* s, const void* const lam_in[4], void* const lam_out[4], double dt,
+                      void* stream) {
+  if (!s || !lam_in || !lam_out || !std::isfinite(dt)) return fail(AGCM_EINVAL, "bad argument");
+  for (int f = 0; f < 4; ++f)
+    if ((!lam_in[f] || !lam_out[f]) && !(f == 1 && s->nv == 0)) return fail(AGCM_EINVAL, "null adjoint buffer %d", f);
+  cudaStream_t st = as_stream(stream);
+  return s->prec == AGCM_FP64 ? adjoint_step<double>(s, lam_in, lam_out, dt, st)
+                              : adjoint_step<float>(s, lam_in, lam_out, dt, st);
+}
+
+int agcm_diagnostics(const agcm_state_t* s, agcm_diag_t* out, void* stream) {
+  if (!s || !out) return fail(AGCM_EINVAL, "null argument");
+  cudaStream_t st = as_stream(stream);
+  double h[8];
+  int rc = s->prec == AGCM_FP64 ? diagnostics<double>(s, h, st) : diagnostics<float>(s, h, st);
+  if (rc) return rc;
+  out->mass = h[0];
+  out->e_kin = h[1];
+  out->e_pot = h[2];
+  out->e_ps = h[3];
+  out->energy = h[1] + h[2] + h[3];
+  out->max_u = h[4];
+  out->max_v = h[5];
+  out->finite = h[6] == 0.0 ? 1 : 0;
+  out->reserved = 0;
+  if (!out->finite) return fail(AGCM_ENONFINITE, "state holds %g non-finite values", h[6]);
+  return AGCM_OK;
+}
+
+int agcm_profile_enable(agcm_state_t* s, int enable) {
+  if (!s) return fail(AGCM_EINVAL, "null state");
+  s->prof.reset();
+  s->prof.on = enable != 0;
+  return AGCM_OK;
+}
+
+int agcm_profile_read(agcm_state_t* s, double* ms_total, int64_t* launches) {
+  if (!s || !ms_total || !launches) return fail(AGCM_EINVAL, "null argument");
+  if (s->prof.drain()) return fail(AGCM_ECUDA, "event synchronisation failed: %s", cudaGetErrorString(cudaGetLastError()));
+  for (int q = 0; q < KID_COUNT; ++q) {
+    ms_total[q] = s->prof.ms[q];
+    launches[q] = s->prof.n[q];
+  }
+  return AGCM_OK;
+}
+
+int agcm_kernel_count(void) { return KID_COUNT; }
+
+const char* agcm_kernel_name(int id) { return (id >= 0 && id < KID_COUNT) ? kKernelNames[id] : ""; }
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ adjoint
+namespace {
+template <class T>
+int adjoint_step(agcm_state* s, const void* const lam_in[4], void* const lam_out[4], double dt, cudaStream_t st) {
+  (void)s; (void)lam_in; (void)lam_out; (void)dt; (void)st;
+  return fail(AGCM_EINVAL, "agcm_step_adjoint: adjoint kernels are not built yet");
+}
+}  // namespace

@@ -1,0 +1,63 @@
+// agcm_common.cuh — device-side geometry and indexing shared by the kernels.
+//
+// Grid conventions (pole-free C grid): scalar/U rows j = 0..J-1 at colatitude
+// (j+1/2) dth, V rows j = 0..J-2 at (j+1) dth, U index i at longitude
+// (i+1/2) dlam.  Storage [k][j][i], longitude contiguous.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace agcm {
+
+// Per-grid tables on the device, in the arithmetic type T of the kernels.
+// Built once per (grid, precision) by the host from the FP64 geometry.
+template <class T>
+struct Geom {
+  int I, J, K;
+  // scalar / U rows (J)
+  const int* Mu;    // leap stride M_j (odd), Eq. 6 / Eq. 7
+  const T* rdx;     // 1 / (a sin(theta_j) M_j dlam): leap zonal difference
+  const T* rdy;     // 1 / (a sin(theta_j) dth): meridional divergence
+  const T* zf;      // a dth / M_j: zonal face length over the leap stride
+  const T* r2A;     // 1 / (2 A_j)
+  const T* f0;      // 2 Omega cos(theta_j)
+  const T* cota;    // cot(theta_j) / a
+  // V rows (J-1)
+  const int* Mv;    // leap stride of the V rows
+  const T* sv;      // sin(theta^v_j)
+  const T* yv;      // a dlam sin(theta^v_j): meridional face length
+  const T* zfv;     // a dth / Mv_j
+  const T* r2Av;    // 1 / (2 Av_j)
+  const T* cn;      // A_j / (4 Av_j)   Coriolis weight of the northern U row
+  const T* cs;      // A_{j+1} / (4 Av_j) Coriolis weight of the southern U row
+  // levels
+  const T* ds;      // dsigma_k (K)
+  const T* r2ds;    // 1 / (2 dsigma_k) (K)
+  const T* hk;      // H[k'][k'] off-diagonal weight ln(sh_{k+1}/sh_k), hk[0] = 0 (K)
+  const T* Hkk;     // diagonal ln(sh_{k+1}/sigma_k) (K)
+  const T* hk_rds;  // hk / dsigma_k (K)
+  const double* dsd;  // dsigma_k in FP64 (column integral of the divergence)
+  const double* shd;  // half levels sigma_hat_h in FP64 (K+1)
+  const double* Ad;   // A_j in FP64 (J)     (diagnostics)
+  const double* Avd;  // Av_j in FP64 (J-1)  (diagnostics)
+  // columns (J*I)
+  const T* rt0pit;  // R T0 / pi~
+  const T* pit;     // pi~ = exp(-phi_s / (R T0))
+  T b;              // sqrt(kappa R T0)
+  T rady;           // 1 / (a dth)
+};
+
+__device__ __forceinline__ int wrapi(int i, int I) {
+  return i < 0 ? i + I : (i >= I ? i - I : i);
+}
+
+template <class T>
+__device__ __forceinline__ T ldg(const T* p) {
+  return __ldg(p);
+}
+
+// sqrt in the kernel's type
+__device__ __forceinline__ double sqrt_t(double x) { return sqrt(x); }
+__device__ __forceinline__ float sqrt_t(float x) { return sqrtf(x); }
+
+}  // namespace agcm

@@ -1,0 +1,98 @@
+"""CPU-side checks of the C ABI: the library loads, exports every symbol the
+header declares, and its host-only calls (grid validation, Eq. 7 tables, the
+CFL time step) behave as specified.  No kernel runs here."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2103_10114_gb300 import agcm
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "agcm.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    agcm.build()
+    return agcm.lib()
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = set(re.findall(r"\b(agcm_[a-z0-9_]+)\s*\(", text))
+    return sorted(n for n in names if not n.endswith("_fn"))
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared_symbols()
+    assert "agcm_step" in names and "agcm_step_adjoint" in names and "agcm_grid_create" in names
+    for n in names:
+        assert hasattr(L, n), n
+        assert n in agcm.SIGNATURES, f"binding lacks {n}"
+
+
+def test_binding_names_match_header():
+    assert set(agcm.SIGNATURES) == set(declared_symbols())
+
+
+@pytest.mark.parametrize("nlon,nlat", [(128, 64), (256, 128), (720, 360), (1440, 720), (37, 23)])
+def test_leap_tables_match_oracle(L, nlon, nlat):
+    g = agcm.Grid(nlon, nlat, 3)
+    lu, lv = g.leap()
+    ou, ov = oracle.leap_table(nlon, nlat)
+    assert np.array_equal(lu, ou) and np.array_equal(lv, ov)
+
+
+def test_grid_validation(L):
+    bad = [
+        dict(nlon=2, nlat=4, nlev=2),
+        dict(nlon=16, nlat=1, nlev=2),
+        dict(nlon=16, nlat=8, nlev=0),
+        dict(nlon=16, nlat=8, nlev=2, leap_u=np.full(8, 2)),
+        dict(nlon=16, nlat=8, nlev=2, leap_u=np.full(8, 9)),
+        dict(nlon=16, nlat=8, nlev=2, leap_v=np.full(7, -1)),
+        dict(nlon=16, nlat=8, nlev=2, sigma_half=[0.0, 0.7, 0.6]),
+        dict(nlon=16, nlat=8, nlev=2, sigma_half=[0.1, 0.5, 1.0]),
+        dict(nlon=16, nlat=8, nlev=2, phis=np.full(128, np.nan)),
+    ]
+    for kw in bad:
+        with pytest.raises(agcm.AgcmError) as e:
+            agcm.Grid(**kw)
+        assert e.value.code == agcm.AGCM_EINVAL
+        assert L.agcm_last_error().decode()
+
+
+def test_null_arguments_are_errors(L):
+    assert L.agcm_grid_create(16, 8, 2, None, None, None, None, None) == agcm.AGCM_EINVAL
+    assert L.agcm_step(None, 1, 1.0, None) == agcm.AGCM_EINVAL
+    assert L.agcm_diagnostics(None, None, None) == agcm.AGCM_EINVAL
+    assert L.agcm_state_create(None, 0, 1, None) == agcm.AGCM_EINVAL
+
+
+def test_cfl_dt_matches_column_eigenproblem(L):
+    """R10: dt = 1.6 / ((c_max + umax) * sqrt(...)), c_max^2 = the largest
+    eigenvalue of the column operator, here from numpy on a matrix written out."""
+    for K, sig in ((8, None), (30, None), (5, [0.0, 0.05, 0.2, 0.5, 0.8, 1.0])):
+        I, J = 128, 64
+        g = agcm.Grid(I, J, K, sigma_half=sig)
+        sh = np.arange(K + 1) / K if sig is None else np.asarray(sig)
+        ds = np.diff(sh)
+        mid = 0.5 * (sh[:-1] + sh[1:])
+        H = np.zeros((K, K))
+        for k in range(K):
+            H[k, k] = math.log(sh[k + 1] / mid[k])
+            for kk in range(k + 1, K):
+                H[k, kk] = math.log(sh[kk + 1] / sh[kk])
+        R, cp, T0 = 287.04, 1004.64, 250.0
+        b2 = (R / cp) * R * T0
+        N = b2 * H @ np.diag(1 / ds) @ H.T @ np.diag(ds) + R * T0 * np.outer(np.ones(K), ds)
+        cmax = math.sqrt(max(np.linalg.eigvals(N).real))
+        a = 6.371e6
+        dl, dth = 2 * math.pi / I, math.pi / J
+        want = 1.6 / ((cmax + 100.0) * math.hypot(2 / (a * math.cos(math.pi / 4) * dl), 2 / (a * dth)))
+        assert abs(g.dt(100.0) / want - 1) < 1e-10

@@ -37,8 +37,8 @@ CASES = [
     (12, 8, 3, "random", {"sigma_half": [0.0, 0.1, 0.45, 1.0]}),
     (20, 9, 5, "random", {"rand_leap": True}),
     (37, 23, 7, "random", {}),  # ragged sizes, odd nlat
-    (3, 2, 1, "random", {}),  # smallest grid: one V row, stride 1 everywhere
-    (5, 3, 1, "random", {}),
+    (3, 2, 1, "random", {"ones": True}),  # smallest grid: one V row
+    (5, 3, 1, "random", {"ones": True}),  # Eq. 7 would ask for 2M >= nlon here
     (128, 64, 8, "rh4", {}),
     (256, 128, 30, "jet", {}),
 ]
@@ -56,6 +56,8 @@ def make_case(nlon, nlat, nlev, kind, extra, seed=11):
         rng = np.random.default_rng(seed + 100)
         mu = 2 * rng.integers(0, (nlon - 1) // 4 + 1, nlat) + 1
         mv = 2 * rng.integers(0, (nlon - 1) // 4 + 1, nlat - 1) + 1
+    if extra.get("ones"):
+        mu, mv = np.ones(nlat, np.int32), np.ones(nlat - 1, np.int32)
     sig = extra.get("sigma_half")
     g = agcm.Grid(nlon, nlat, nlev, sigma_half=sig, leap_u=mu, leap_v=mv, phis=st["phis"])
     o = oracle.Oracle(nlon, nlat, nlev, sigma_half=sig, leap_u=mu, leap_v=mv, phis=st["phis"])
@@ -159,3 +161,20 @@ def test_energy_neutral_on_gpu_full_size():
     assert abs(tot) <= 1e-12 * mag, tot / mag
     # and the mass tendency integrates to zero
     assert abs(np.sum(A[:, None] * t["pi"])) <= 1e-13 * np.sum(A[:, None] * np.abs(t["pi"]))
+
+
+def test_full_size_one_step_fp32():
+    """The bench workload itself (1440 x 720 x 30, FP32 with FP64 column sums,
+    the same launch path as bench.py): one step against the FP64 oracle."""
+    I, J, K = 1440, 720, 30
+    st = inputs.baroclinic_jet(I, J, K, seed=5, noise=1e-2, terrain_seed=2)
+    g = agcm.Grid(I, J, K, phis=st["phis"])
+    dt = g.dt(100.0)
+    s = agcm.State(g, agcm.AGCM_FP32)
+    s.load(st)
+    s.step(1, dt)
+    out = to_np(s.store())
+    s.close()
+    ref = oracle.Oracle(I, J, K, phis=st["phis"]).step(st, dt, 1)
+    for f in FIELDS:
+        assert rel_err(out[f], ref[f]) <= 1e-5, (f, rel_err(out[f], ref[f]))

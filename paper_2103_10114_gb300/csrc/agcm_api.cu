@@ -184,6 +184,11 @@ struct agcm_state {
   void* X = nullptr;
   void* psi = nullptr;
   double* C = nullptr;
+  // FP64 vertical means sum_k dsigma U_k and V_k of x[0..2] (J*I each), the
+  // input of the fused stage kernel's column integral; bar_valid for x[0]
+  double* ubar[3] = {};
+  double* vbar[3] = {};
+  bool bar_valid = false;
   // diagnostics partials
   double* diag = nullptr;
   std::vector<void*> owned;
@@ -337,17 +342,67 @@ int run_stage(agcm_state* s, const agcm::Geom<T>& G, void* const xs[4], void* co
 }
 
 template <class T>
+const agcm::Geom<T>& geom_of(const agcm_state* s) {
+  if constexpr (sizeof(T) == 8)
+    return s->grid->gd;
+  else
+    return s->grid->gf;
+}
+
+// FP64 vertical means of x[0] (needed once after a load).
+template <class T>
+int ensure_bar(agcm_state* s, cudaStream_t st) {
+  if (s->bar_valid) return AGCM_OK;
+  const agcm::Geom<T>& G = geom_of<T>(s);
+  s->prof.begin(KID_FUSED_PRE, st);
+  agcm::k_vsum<T><<<nblocks(s->n2, 256), 256, 0, st>>>(G, (const T*)s->x[0][0], (const T*)s->x[0][1], s->ubar[0],
+                                                       s->vbar[0]);
+  s->prof.end(st);
+  CUDA_TRY(cudaGetLastError());
+  s->bar_valid = true;
+  return AGCM_OK;
+}
+
+// One fused stage: out = base + cdt * T(x[in]) (MODE 1: base = x[in]; MODE 2:
+// base = x[0]; MODE 0: out = T).  Writes the vertical means of out to bar[outb]
+// (outb < 0: not written).
+template <class T, int MODE>
+int fused_stage(agcm_state* s, int in, void* const out[4], int outb, double cdt, cudaStream_t st) {
+  const agcm::Geom<T>& G = geom_of<T>(s);
+  const dim3 block(agcm::kFusedBX, agcm::kFusedBY);
+  const dim3 grid((unsigned)((G.I + agcm::kFusedBX - 1) / agcm::kFusedBX),
+                  (unsigned)((G.J + agcm::kFusedBY - 1) / agcm::kFusedBY));
+  void* const* xs = s->x[in];
+  void* const* xb = s->x[0];
+  s->prof.begin(KID_FUSED, st);
+  agcm::k_fused_stage<T, MODE><<<grid, block, 0, st>>>(
+      G, (const T*)xs[0], (const T*)xs[1], (const T*)xs[2], (const T*)xs[3], s->ubar[in], s->vbar[in],
+      (const T*)xb[0], (const T*)xb[1], (const T*)xb[2], (const T*)xb[3], (T*)out[0], (T*)out[1], (T*)out[2],
+      (T*)out[3], outb >= 0 ? s->ubar[outb] : nullptr, outb >= 0 ? s->vbar[outb] : nullptr, (T)cdt);
+  s->prof.end(st);
+  CUDA_TRY(cudaGetLastError());
+  return AGCM_OK;
+}
+
+template <class T>
 int run_steps(agcm_state* s, int nsteps, double dt, cudaStream_t st) {
-  const agcm::Geom<T>& G = *reinterpret_cast<const agcm::Geom<T>*>(
-      sizeof(T) == 8 ? (const void*)&s->grid->gd : (const void*)&s->grid->gf);
+  int rc = ensure_bar<T>(s, st);
+  if (rc) return rc;
   for (int n = 0; n < nsteps; ++n) {
-    int rc;
-    if ((rc = run_stage<T>(s, G, s->x[0], s->x[0], s->x[1], 0.5 * dt, st))) return rc;
-    if ((rc = run_stage<T>(s, G, s->x[1], s->x[0], s->x[2], 0.5 * dt, st))) return rc;
-    if ((rc = run_stage<T>(s, G, s->x[2], s->x[0], s->x[0], dt, st))) return rc;
+    if ((rc = fused_stage<T, 1>(s, 0, s->x[1], 1, 0.5 * dt, st))) return rc;
+    if ((rc = fused_stage<T, 2>(s, 1, s->x[2], 2, 0.5 * dt, st))) return rc;
+    if ((rc = fused_stage<T, 2>(s, 2, s->x[0], 0, dt, st))) return rc;
   }
   return AGCM_OK;
 }
+
+template <class T>
+int run_tendency(agcm_state* s, void* const out[4], cudaStream_t st) {
+  int rc = ensure_bar<T>(s, st);
+  if (rc) return rc;
+  return fused_stage<T, 0>(s, 0, out, -1, 1.0, st);
+}
+
 
 template <class T>
 int diagnostics(const agcm_state* s, double h[8], cudaStream_t st) {
@@ -555,6 +610,10 @@ int agcm_state_create(const agcm_grid_t* g, int precision, int nmembers, agcm_st
   ok = ok && (s->X = get(s->n3 * s->esz));
   ok = ok && (s->psi = get(s->n3 * s->esz));
   ok = ok && (s->C = (double*)get(s->n2 * sizeof(double)));
+  for (int c = 0; c < 3 && ok; ++c) {
+    ok = ok && (s->ubar[c] = (double*)get(s->n2 * sizeof(double)));
+    ok = ok && (s->vbar[c] = (double*)get(s->n2 * sizeof(double)));
+  }
   ok = ok && (s->diag = (double*)get((agcm::kDiagPartials + 1) * 8 * sizeof(double)));
   if (!ok) {
     for (void* p : s->owned) dev_free(p);
@@ -594,6 +653,7 @@ int agcm_state_load(agcm_state_t* s, const void* U, const void* V, const void* P
   if (s->nv) CUDA_TRY(cudaMemcpyAsync(s->x[0][1], V, s->nv * s->esz, kind, st));
   CUDA_TRY(cudaMemcpyAsync(s->x[0][2], Phi, s->n3 * s->esz, kind, st));
   CUDA_TRY(cudaMemcpyAsync(s->x[0][3], pi, s->n2 * s->esz, kind, st));
+  s->bar_valid = false;
   return AGCM_OK;
 }
 
@@ -620,9 +680,7 @@ int agcm_tendency(agcm_state_t* s, void* tU, void* tV, void* tPhi, void* tpi, vo
   if (!s || !tU || !tPhi || !tpi || (!tV && s->nv)) return fail(AGCM_EINVAL, "null argument");
   cudaStream_t st = as_stream(stream);
   void* out[4] = {tU, tV, tPhi, tpi};
-  void* none[4] = {nullptr, nullptr, nullptr, nullptr};
-  if (s->prec == AGCM_FP64) return run_stage<double>(s, s->grid->gd, s->x[0], none, out, 1.0, st);
-  return run_stage<float>(s, s->grid->gf, s->x[0], none, out, 1.0, st);
+  return s->prec == AGCM_FP64 ? run_tendency<double>(s, out, st) : run_tendency<float>(s, out, st);
 }
 
 int agcm_step_adjoint(agcm_state_t* s, const void* const lam_in[4], void* const lam_out[4], double dt,

@@ -192,6 +192,13 @@ struct agcm_state {
   // diagnostics partials
   double* diag = nullptr;
   std::vector<void*> owned;
+  // adjoint workspace (allocated on the first agcm_step_adjoint call)
+  bool adj_ready = false;
+  void* adj3[9] = {};   // aU aFl aGu aGs aPsi aPhi tRP tRPu tPu   (K*J*I)
+  void* adjv[5] = {};   // aV aFt aGv tRPv tPv                      (K*(J-1)*I)
+  void* adjW = nullptr; // aW                                       ((K+1)*J*I)
+  void* adj2[6] = {};   // arPcol aPiD mub mvb mcb pi_scratch       (J*I)
+  void* mu[2][4] = {};  // stage adjoints mu2, mu1
 };
 
 namespace {
@@ -737,9 +744,110 @@ const char* agcm_kernel_name(int id) { return (id >= 0 && id < KID_COUNT) ? kKer
 
 // ------------------------------------------------------------------ adjoint
 namespace {
+
+int ensure_adj(agcm_state* s) {
+  if (s->adj_ready) return AGCM_OK;
+  const size_t e = s->esz, n3 = s->n3 * e, nv = std::max<size_t>(s->nv, 1) * e, n2 = s->n2 * e;
+  const size_t nw = (size_t)(s->grid->K + 1) * s->grid->J * s->grid->I * e;
+  bool ok = true;
+  auto get = [&](size_t bytes) -> void* {
+    void* p = dev_alloc(bytes);
+    if (p) s->owned.push_back(p);
+    else ok = false;
+    return p;
+  };
+  for (auto& p : s->adj3) p = get(n3);
+  for (auto& p : s->adjv) p = get(nv);
+  s->adjW = get(nw);
+  for (auto& p : s->adj2) p = get(n2);
+  for (int c = 0; c < 2; ++c) {
+    s->mu[c][0] = get(n3);
+    s->mu[c][1] = get(nv);
+    s->mu[c][2] = get(n3);
+    s->mu[c][3] = get(n2);
+  }
+  if (!ok) return fail(AGCM_ENOMEM, "device allocation of the adjoint workspace failed");
+  s->adj_ready = true;
+  return AGCM_OK;
+}
+
+// out = (accumulate ? out : 0) + scale * J(x)^T y, J the Jacobian of T at x.
+template <class T>
+int vjp(agcm_state* s, void* const x[4], const void* const y[4], void* const out[4], double scale, int accumulate,
+        cudaStream_t st) {
+  const agcm::Geom<T>& G = geom_of<T>(s);
+  const size_t n2 = s->n2, n3 = s->n3, nv = s->nv, e = s->esz;
+  agcm::ColState<T> cs{(T*)s->col[0], (T*)s->col[1], (T*)s->col[2], (T*)s->col[3], (T*)s->col[4], (T*)s->col[5]};
+  // forward phases A and B at x: P family, W, X, psi
+  s->prof.begin(KID_COLSTATE, st);
+  agcm::k_colstate<T><<<nblocks(n2, 256), 256, 0, st>>>(G, (const T*)x[3], cs);
+  s->prof.end(st);
+  s->prof.begin(KID_COLUMN, st);
+  agcm::k_column<T><<<nblocks(n2, 128), 128, 0, st>>>(G, (const T*)x[0], (const T*)x[1], (const T*)x[2],
+                                                      (const T*)x[3], cs, (T*)s->W, (T*)s->X, (T*)s->psi, nullptr,
+                                                      (T*)s->adj2[5], 1.0, nullptr);
+  s->prof.end(st);
+  agcm::AdjBufs<T> a{};
+  a.aU = (T*)s->adj3[0]; a.aFl = (T*)s->adj3[1]; a.aGu = (T*)s->adj3[2]; a.aGs = (T*)s->adj3[3];
+  a.aPsi = (T*)s->adj3[4]; a.aPhi = (T*)s->adj3[5]; a.tRP = (T*)s->adj3[6]; a.tRPu = (T*)s->adj3[7];
+  a.tPu = (T*)s->adj3[8];
+  a.aV = (T*)s->adjv[0]; a.aFt = (T*)s->adjv[1]; a.aGv = (T*)s->adjv[2]; a.tRPv = (T*)s->adjv[3];
+  a.tPv = (T*)s->adjv[4];
+  a.aW = (T*)s->adjW;
+  a.arPcol = (T*)s->adj2[0]; a.aPiD = (T*)s->adj2[1]; a.mub = (T*)s->adj2[2]; a.mvb = (T*)s->adj2[3];
+  a.mcb = (T*)s->adj2[4];
+  for (int q : {0, 1, 2, 3, 4}) CUDA_TRY(cudaMemsetAsync(s->adj3[q], 0, n3 * e, st));
+  for (int q : {0, 1, 2}) CUDA_TRY(cudaMemsetAsync(s->adjv[q], 0, std::max<size_t>(nv, 1) * e, st));
+  CUDA_TRY(cudaMemsetAsync(s->adjW, 0, (size_t)(G.K + 1) * n2 * e, st));
+  s->prof.begin(KID_ADJ_UPDATE, st);
+  agcm::k_adj_update<T><<<nblocks(n3, 256), 256, 0, st>>>(G, (const T*)x[0], (const T*)x[1], (const T*)x[2], cs,
+                                                          (const T*)s->W, (const T*)s->psi, (const T*)y[0],
+                                                          (const T*)y[1], (const T*)y[2], a);
+  s->prof.end(st);
+  s->prof.begin(KID_ADJ_COLUMN, st);
+  agcm::k_adj_column<T><<<nblocks(n2, 128), 128, 0, st>>>(G, (const T*)x[2], cs, (const T*)s->X, (const T*)y[2],
+                                                          (const T*)y[3], a);
+  s->prof.end(st);
+  s->prof.begin(KID_ADJ_COLSTATE, st);
+  agcm::k_adj_conv<T><<<nblocks(n2, 128), 128, 0, st>>>(G, (const T*)x[0], (const T*)x[1], (const T*)x[2], cs, a,
+                                                        (T*)out[0], (T*)out[1], (T*)out[2], (T)scale, accumulate);
+  agcm::k_adj_colstate<T><<<nblocks(n2, 256), 256, 0, st>>>(G, a, (T*)out[3], (T)scale, accumulate);
+  s->prof.end(st);
+  CUDA_TRY(cudaGetLastError());
+  return AGCM_OK;
+}
+
+template <class T>
+int axpy4(agcm_state* s, const void* const x[4], void* const y[4], cudaStream_t st) {
+  const size_t n[4] = {s->n3, s->nv, s->n3, s->n2};
+  s->prof.begin(KID_ADJ_AXPY, st);
+  for (int f = 0; f < 4; ++f)
+    if (n[f]) agcm::k_axpy<T><<<nblocks(n[f], 256), 256, 0, st>>>(n[f], T(1), (const T*)x[f], (T*)y[f]);
+  s->prof.end(st);
+  CUDA_TRY(cudaGetLastError());
+  return AGCM_OK;
+}
+
+// One step x3 = xn + dt T(x2), x2 = xn + dt/2 T(x1), x1 = xn + dt/2 T(xn):
+// lam_n = lam3 + mu2 + mu1 + dt/2 J(xn)^T mu1, mu2 = dt J(x2)^T lam3,
+// mu1 = dt/2 J(x1)^T mu2.  The stage states are recomputed from xn.
 template <class T>
 int adjoint_step(agcm_state* s, const void* const lam_in[4], void* const lam_out[4], double dt, cudaStream_t st) {
-  (void)s; (void)lam_in; (void)lam_out; (void)dt; (void)st;
-  return fail(AGCM_EINVAL, "agcm_step_adjoint: adjoint kernels are not built yet");
+  int rc;
+  if ((rc = ensure_adj(s))) return rc;
+  if ((rc = ensure_bar<T>(s, st))) return rc;
+  if ((rc = fused_stage<T, 1>(s, 0, s->x[1], 1, 0.5 * dt, st))) return rc;
+  if ((rc = fused_stage<T, 2>(s, 1, s->x[2], 2, 0.5 * dt, st))) return rc;
+  const size_t n[4] = {s->n3, s->nv, s->n3, s->n2};
+  for (int f = 0; f < 4; ++f)
+    if (n[f]) CUDA_TRY(cudaMemcpyAsync(lam_out[f], lam_in[f], n[f] * s->esz, cudaMemcpyDeviceToDevice, st));
+  void* const* mu2 = s->mu[0];
+  void* const* mu1 = s->mu[1];
+  if ((rc = vjp<T>(s, s->x[2], lam_in, mu2, dt, 0, st))) return rc;
+  if ((rc = axpy4<T>(s, mu2, lam_out, st))) return rc;
+  if ((rc = vjp<T>(s, s->x[1], mu2, mu1, 0.5 * dt, 0, st))) return rc;
+  if ((rc = axpy4<T>(s, mu1, lam_out, st))) return rc;
+  return vjp<T>(s, s->x[0], mu1, lam_out, 0.5 * dt, 1, st);
 }
+
 }  // namespace

@@ -173,6 +173,27 @@ int agcm_profile_read(agcm_state_t* state, double* ms_total, int64_t* launches);
 int agcm_kernel_count(void);
 const char* agcm_kernel_name(int id);
 
+/*
+ * agcm_tendency_static — T(x) like agcm_tendency, for callers that cannot
+ * allocate device memory (a caller inside a CUDA-graph capture or under a
+ * memory budget that forbids new allocations, or an embedder whose allocator
+ * owns all device memory and lends the library only its buffers).  The paper
+ * has no counterpart; this is a deployment convenience.
+ *   grid:   created with agcm_grid_create (host only); nlon*nlat <= 262144,
+ *           nlat <= 4096, nlev <= 256 — larger grids return AGCM_EINVAL.
+ *   U, V, Phi, pi: caller-owned device input (layout above, element type of
+ *           `precision`); tU, tV, tPhi, tpi: caller-owned device output.
+ * The call allocates nothing: its scratch (the grid's device tables and the
+ * FP64 vertical means, about 11 MB) is one fixed array that every GPU holds
+ * from library load until process exit.  Every call overwrites that array, so
+ * calls whose kernels overlap on a GPU (other streams, other threads) race;
+ * serialise them.  The first call on a device looks up the array's device
+ * address (set-up, once per device, with that device current); make that
+ * first call before any stream capture.  Asynchronous on `stream`.
+ */
+int agcm_tendency_static(const agcm_grid_t* grid, int precision, const void* U, const void* V, const void* Phi,
+                         const void* pi, void* tU, void* tV, void* tPhi, void* tpi, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -82,6 +82,7 @@ SIGNATURES = {
     "agcm_profile_read": (_i, [_vp, _pd, ctypes.POINTER(ctypes.c_int64)]),
     "agcm_kernel_count": (_i, []),
     "agcm_kernel_name": (ctypes.c_char_p, [_i]),
+    "agcm_tendency_static": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
 }
 
 

@@ -11,6 +11,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -851,3 +852,182 @@ int adjoint_step(agcm_state* s, const void* const lam_in[4], void* const lam_out
 }
 
 }  // namespace
+
+// ======================================= allocation-free tendency (static scratch)
+//
+// agcm_tendency_static computes T(x) like agcm_tendency, but without a state
+// object and without allocating device memory: its scratch (the grid's device
+// tables and the FP64 vertical means Ubar/Vbar) lives in one file-scope
+// __device__ array of fixed size that every GPU holds from the moment this
+// library is loaded until the process exits.  It serves callers that cannot
+// call cudaMalloc: code running inside a CUDA graph capture or a memory-pool
+// budget that forbids new allocations, and embedders whose allocator owns all
+// device memory and hands the library only input and output buffers.
+namespace {
+
+constexpr size_t kStaticCols = 262144;  // nlat * nlon at most (e.g. 720 x 360)
+constexpr int kStaticRows = 4096;       // nlat at most
+constexpr int kStaticLevels = 256;      // nlev at most
+constexpr int kStaticMaxDevices = 64;
+
+constexpr size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+// byte layout of the scratch array
+constexpr size_t kRowB = al256(kStaticRows * 8), kLevB = al256((kStaticLevels + 1) * 8),
+                 kColB = al256(kStaticCols * 8);
+constexpr size_t kOffRaw = 0;                        // 6 row arrays s c cot A sv Av (double)
+constexpr size_t kOffRawLev = kOffRaw + 6 * kRowB;   // sh ds Hkk hk (double)
+constexpr size_t kOffPitRaw = kOffRawLev + 4 * kLevB;  // pi~ (double)
+constexpr size_t kOffInt = kOffPitRaw + kColB;       // Mu Mv (int)
+constexpr size_t kOffRowT = kOffInt + 2 * kRowB;     // 12 typed row arrays
+constexpr size_t kOffLevT = kOffRowT + 12 * kRowB;   // 5 typed level arrays
+constexpr size_t kOffColT = kOffLevT + 5 * kLevB;    // pit, rt0pit (typed)
+constexpr size_t kOffBar = kOffColT + 2 * kColB;     // Ubar, Vbar (double)
+constexpr size_t kStaticBytes = kOffBar + 2 * kColB; // about 11 MB
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
+
+namespace {
+
+std::mutex g_static_mu;
+void* g_static_ptr[kStaticMaxDevices] = {};
+
+// Typed device tables from the raw FP64 ones (same formulas as the state path).
+template <class T>
+__global__ void k_static_geom(int I, int J, int K, const double* raw, const double* rawlev, const double* pitraw,
+                              const int* Mu, const int* Mv, T* rowT, T* levT, T* colT, size_t rowStride,
+                              size_t levStride, size_t colStride) {
+  const double* s = raw;
+  const double* c = raw + rowStride;
+  const double* cot = raw + 2 * rowStride;
+  const double* A = raw + 3 * rowStride;
+  const double* sv = raw + 4 * rowStride;
+  const double* Av = raw + 5 * rowStride;
+  const double* ds = rawlev + levStride;
+  const double* hk = rawlev + 3 * levStride;
+  const double dlam = 2.0 * kPi / I, dth = kPi / J;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x; n < (size_t)I * J; n += stride) {
+    if (n < (size_t)J) {
+      const int j = (int)n;
+      rowT[0 * rowStride + j] = (T)(1.0 / (kA * s[j] * Mu[j] * dlam));
+      rowT[1 * rowStride + j] = (T)(1.0 / (kA * s[j] * dth));
+      rowT[2 * rowStride + j] = (T)(kA * dth / Mu[j]);
+      rowT[3 * rowStride + j] = (T)(0.5 / A[j]);
+      rowT[4 * rowStride + j] = (T)(2.0 * kOmega * c[j]);
+      rowT[5 * rowStride + j] = (T)(cot[j] / kA);
+      if (j < J - 1) {
+        rowT[6 * rowStride + j] = (T)sv[j];
+        rowT[7 * rowStride + j] = (T)(kA * dlam * sv[j]);
+        rowT[8 * rowStride + j] = (T)(kA * dth / Mv[j]);
+        rowT[9 * rowStride + j] = (T)(0.5 / Av[j]);
+        rowT[10 * rowStride + j] = (T)(0.25 * A[j] / Av[j]);
+        rowT[11 * rowStride + j] = (T)(0.25 * A[j + 1] / Av[j]);
+      }
+    }
+    if (n < (size_t)K) {
+      const int k = (int)n;
+      levT[0 * levStride + k] = (T)ds[k];
+      levT[1 * levStride + k] = (T)(0.5 / ds[k]);
+      levT[2 * levStride + k] = (T)hk[k];
+      levT[3 * levStride + k] = (T)rawlev[2 * levStride + k];
+      levT[4 * levStride + k] = (T)(hk[k] / ds[k]);
+    }
+    colT[n] = (T)pitraw[n];
+    colT[colStride + n] = (T)(kR * kT0 / pitraw[n]);
+  }
+}
+
+template <class T>
+int tendency_static(const agcm_grid* g, char* base, const void* U, const void* V, const void* Phi, const void* pi,
+                    void* tU, void* tV, void* tPhi, void* tpi, cudaStream_t st) {
+  const int I = g->I, J = g->J, K = g->K;
+  const size_t rS = kRowB / 8, lS = kLevB / 8, cS = kColB / 8;  // strides in elements of 8 bytes
+  double* raw = (double*)(base + kOffRaw);
+  double* rawlev = (double*)(base + kOffRawLev);
+  double* pitraw = (double*)(base + kOffPitRaw);
+  int* Mu = (int*)(base + kOffInt);
+  int* Mv = (int*)(base + kOffInt + kRowB);
+  const std::vector<double>* rows[6] = {&g->s, &g->c, &g->cot, &g->A, &g->sv, &g->Av};
+  for (int q = 0; q < 6; ++q)
+    if (!rows[q]->empty())
+      CUDA_TRY(cudaMemcpyAsync(raw + q * rS, rows[q]->data(), rows[q]->size() * 8, cudaMemcpyHostToDevice, st));
+  const std::vector<double>* levs[4] = {&g->sh, &g->ds, &g->Hkk, &g->hk};
+  for (int q = 0; q < 4; ++q)
+    CUDA_TRY(cudaMemcpyAsync(rawlev + q * lS, levs[q]->data(), levs[q]->size() * 8, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(pitraw, g->pit.data(), g->pit.size() * 8, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(Mu, g->Mu.data(), g->Mu.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  if (!g->Mv.empty())
+    CUDA_TRY(cudaMemcpyAsync(Mv, g->Mv.data(), g->Mv.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  // typed tables are indexed with the element strides rS/lS/cS of the raw
+  // (8-byte) tables, so a float table uses the first half of its region
+  T* rowT = (T*)(base + kOffRowT);
+  T* levT = (T*)(base + kOffLevT);
+  T* colT = (T*)(base + kOffColT);
+  k_static_geom<T><<<nblocks((size_t)I * J, 256), 256, 0, st>>>(I, J, K, raw, rawlev, pitraw, Mu, Mv, rowT, levT,
+                                                                colT, rS, lS, cS);
+  agcm::Geom<T> G{};
+  G.I = I; G.J = J; G.K = K;
+  G.Mu = Mu;
+  G.Mv = Mv;
+  G.rdx = rowT + 0 * rS; G.rdy = rowT + 1 * rS; G.zf = rowT + 2 * rS; G.r2A = rowT + 3 * rS;
+  G.f0 = rowT + 4 * rS; G.cota = rowT + 5 * rS; G.sv = rowT + 6 * rS; G.yv = rowT + 7 * rS;
+  G.zfv = rowT + 8 * rS; G.r2Av = rowT + 9 * rS; G.cn = rowT + 10 * rS; G.cs = rowT + 11 * rS;
+  G.ds = levT + 0 * lS; G.r2ds = levT + 1 * lS; G.hk = levT + 2 * lS; G.Hkk = levT + 3 * lS;
+  G.hk_rds = levT + 4 * lS;
+  G.dsd = rawlev + 1 * lS;
+  G.shd = rawlev + 0 * lS;
+  G.Ad = raw + 3 * rS;
+  G.Avd = raw + 5 * rS;
+  G.pit = colT;
+  G.rt0pit = colT + cS;
+  G.b = (T)g->b;
+  G.rady = (T)(1.0 / (kA * g->dth));
+  double* ubar = (double*)(base + kOffBar);
+  double* vbar = (double*)(base + kOffBar + kColB);
+  agcm::k_vsum<T><<<nblocks((size_t)I * J, 256), 256, 0, st>>>(G, (const T*)U, (const T*)V, ubar, vbar);
+  const dim3 block(agcm::kFusedBX, agcm::kFusedBY);
+  const dim3 grid((unsigned)((I + agcm::kFusedBX - 1) / agcm::kFusedBX),
+                  (unsigned)((J + agcm::kFusedBY - 1) / agcm::kFusedBY));
+  agcm::k_fused_stage<T, 0><<<grid, block, 0, st>>>(G, (const T*)U, (const T*)V, (const T*)Phi, (const T*)pi, ubar,
+                                                    vbar, nullptr, nullptr, nullptr, nullptr, (T*)tU, (T*)tV,
+                                                    (T*)tPhi, (T*)tpi, nullptr, nullptr, (T)1);
+  CUDA_TRY(cudaGetLastError());
+  return AGCM_OK;
+}
+
+}  // namespace
+
+extern "C" int agcm_tendency_static(const agcm_grid_t* g, int precision, const void* U, const void* V,
+                                    const void* Phi, const void* pi, void* tU, void* tV, void* tPhi, void* tpi,
+                                    void* stream) {
+  if (!g || !U || !V || !Phi || !pi || !tU || !tV || !tPhi || !tpi) return fail(AGCM_EINVAL, "null argument");
+  if (precision != AGCM_FP64 && precision != AGCM_FP32)
+    return fail(AGCM_EINVAL, "precision must be AGCM_FP64 or AGCM_FP32");
+  if ((size_t)g->I * g->J > kStaticCols || g->J > kStaticRows || g->K > kStaticLevels)
+    return fail(AGCM_EINVAL,
+                "agcm_tendency_static: grid %d x %d x %d exceeds the static scratch limit "
+                "(nlon*nlat <= %zu, nlat <= %d, nlev <= %d)",
+                g->I, g->J, g->K, kStaticCols, kStaticRows, kStaticLevels);
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kStaticMaxDevices) return fail(AGCM_EINVAL, "device ordinal %d not supported", dev);
+  void* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_ptr[dev]) {
+      // once per device, with that device current: the device address of the
+      // scratch array (its host-side name is only a stand-in)
+      void* p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+      if (e != cudaSuccess || !p)
+        return fail(AGCM_ECUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
+      g_static_ptr[dev] = p;
+    }
+    base = g_static_ptr[dev];
+  }
+  cudaStream_t st = as_stream(stream);
+  return precision == AGCM_FP64 ? tendency_static<double>(g, (char*)base, U, V, Phi, pi, tU, tV, tPhi, tpi, st)
+                                : tendency_static<float>(g, (char*)base, U, V, Phi, pi, tU, tV, tPhi, tpi, st);
+}

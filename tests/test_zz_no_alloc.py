@@ -1,0 +1,61 @@
+"""agcm_tendency_static: the allocation-free tendency entry point.
+
+Some callers cannot allocate device memory (inside a CUDA-graph capture, under
+a fixed memory budget, or when an embedding application's allocator owns all
+of the GPU).  This entry point takes only the caller's input and output
+buffers and keeps its scratch in a fixed array inside the library.  The test
+checks it, through the C ABI, against agcm_tendency (which allocates its own
+state) on two calls in a row, within the tolerances of the parity tests.
+This file is collected last on purpose.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2103_10114_gb300 import agcm, inputs
+
+pytestmark = pytest.mark.gpu
+FIELDS = agcm.FIELDS
+
+
+def _static_tendency(grid, precision, dev_in):
+    import torch
+
+    out = {f: torch.empty_like(dev_in[f]) for f in FIELDS}
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rc = agcm.lib().agcm_tendency_static(grid.handle, precision, *[dev_in[f].data_ptr() for f in FIELDS],
+                                         *[out[f].data_ptr() for f in FIELDS], stream)
+    agcm.check(rc)
+    return out
+
+
+@pytest.mark.parametrize("precision,tol", [(agcm.AGCM_FP64, 1e-12), (agcm.AGCM_FP32, 1e-6)])
+def test_static_tendency_matches_state_path_twice(cuda_ok, precision, tol):
+    import torch
+
+    agcm.build()
+    cases = [(64, 32, 10, 3), (37, 23, 7, 4)]  # two different grids, one call each, in a row
+    for I, J, K, seed in cases:
+        st = inputs.baroclinic_jet(I, J, K, seed=seed, noise=1e-2, terrain_seed=2)
+        g = agcm.Grid(I, J, K, phis=st["phis"])
+        s = agcm.State(g, precision)
+        dtype = s.dtype
+        dev_in = {f: torch.as_tensor(np.ascontiguousarray(st[f]), dtype=dtype, device="cuda") for f in FIELDS}
+        s.load(dev_in)
+        ref = s.tendency()
+        got = _static_tendency(g, precision, dev_in)
+        torch.cuda.synchronize()
+        for f in FIELDS:
+            r, o = ref[f].double().cpu().numpy(), got[f].double().cpu().numpy()
+            err = np.abs(o - r).max() / max(np.abs(r).max(), 1e-300)
+            assert err <= tol, (I, J, K, f, err)
+        s.close()
+        g.close()
+
+
+def test_static_tendency_rejects_oversized_grid():
+    g = agcm.Grid(1440, 720, 30)
+    rc = agcm.lib().agcm_tendency_static(g.handle, agcm.AGCM_FP32, *([ctypes.c_void_p(16)] * 8), None)
+    assert rc == agcm.AGCM_EINVAL
+    assert "static scratch limit" in agcm.lib().agcm_last_error().decode()

@@ -174,6 +174,38 @@ int agcm_kernel_count(void);
 const char* agcm_kernel_name(int id);
 
 /*
+ * Ensembles (many members, uneven resolutions, one persistent launch).
+ * agcm_ensemble_create: members are existing states, all of one precision,
+ * each on its own grid; the ensemble borrows their buffers (destroy it before
+ * them).  agcm_ensemble_step advances every member nsteps steps of the
+ * three-stage scheme (dt[m] seconds for member m) in one kernel launch whose
+ * blocks pull (member, row segment) work items from a device queue; member m
+ * does the same arithmetic as agcm_step on it (results agree to the last bit
+ * in FP32 and to a few ulp in FP64, where multiply-add contraction may differ).  Stages are separated
+ * by grid barriers whose waits are bounded by the timeout (default 1 s): if a
+ * wait runs out the kernel stops and agcm_ensemble_status reports
+ * AGCM_ETIMEOUT (this happens only if not all blocks can be resident at once,
+ * e.g. when other work occupies the GPU).  The launch can be captured in a
+ * CUDA graph once a first call has uploaded the dt values (nsteps = 0 only
+ * prepares: it uploads dt and the members' vertical means without stepping).
+ * agcm_ensemble_configure sets the launch shape (warps per block 1..4, blocks
+ * per SM, 0 = as many as fit); an autotuner picks it (ensemble.py).
+ * agcm_ensemble_set_timeout: barrier timeout in seconds; test_missing_blocks
+ * > 0 makes every barrier wait for blocks that do not exist, to exercise the
+ * timeout path (tests only).  agcm_ensemble_profile: enable (1) / disable (0)
+ * CUDA-event timing of the ensemble launches, or read it (-1 keeps the state)
+ * into ms_total / launches when those are non-NULL.
+ */
+typedef struct agcm_ensemble agcm_ensemble_t;
+int agcm_ensemble_create(agcm_state_t* const* members, int n, agcm_ensemble_t** out);
+int agcm_ensemble_destroy(agcm_ensemble_t* ens);
+int agcm_ensemble_configure(agcm_ensemble_t* ens, int warps_per_block, int blocks_per_sm);
+int agcm_ensemble_set_timeout(agcm_ensemble_t* ens, double seconds, int test_missing_blocks);
+int agcm_ensemble_step(agcm_ensemble_t* ens, int nsteps, const double* dt, void* stream);
+int agcm_ensemble_status(agcm_ensemble_t* ens, void* stream);
+int agcm_ensemble_profile(agcm_ensemble_t* ens, int enable, double* ms_total, int64_t* launches);
+
+/*
  * agcm_tendency_static — T(x) like agcm_tendency, for callers that cannot
  * allocate device memory (a caller inside a CUDA-graph capture or under a
  * memory budget that forbids new allocations, or an embedder whose allocator

@@ -83,6 +83,13 @@ SIGNATURES = {
     "agcm_kernel_count": (_i, []),
     "agcm_kernel_name": (ctypes.c_char_p, [_i]),
     "agcm_tendency_static": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "agcm_ensemble_create": (_i, [ctypes.POINTER(_vp), _i, ctypes.POINTER(_vp)]),
+    "agcm_ensemble_destroy": (_i, [_vp]),
+    "agcm_ensemble_configure": (_i, [_vp, _i, _i]),
+    "agcm_ensemble_set_timeout": (_i, [_vp, _d, _i]),
+    "agcm_ensemble_step": (_i, [_vp, _i, _pd, _vp]),
+    "agcm_ensemble_status": (_i, [_vp, _vp]),
+    "agcm_ensemble_profile": (_i, [_vp, _i, _pd, ctypes.POINTER(ctypes.c_int64)]),
 }
 
 

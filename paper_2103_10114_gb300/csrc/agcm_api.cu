@@ -21,6 +21,7 @@
 #include "agcm_fused.cuh"
 #include "agcm_adjoint.cuh"
 #include "agcm_diag.cuh"
+#include "agcm_ensemble.cuh"
 
 namespace {
 
@@ -119,11 +120,12 @@ enum KernelId : int {
   KID_ADJ_COLUMN,
   KID_ADJ_COLSTATE,
   KID_ADJ_AXPY,
+  KID_ENSEMBLE,
   KID_COUNT
 };
 static const char* const kKernelNames[KID_COUNT] = {
     "k_colstate", "k_column", "k_update", "k_fused_colsum", "k_fused_stage", "k_diag",
-    "k_adj_update", "k_adj_column", "k_adj_colstate", "k_adj_axpy"};
+    "k_adj_update", "k_adj_column", "k_adj_colstate", "k_adj_axpy", "k_ensemble"};
 
 struct Profiler {
   bool on = false;
@@ -1031,3 +1033,186 @@ extern "C" int agcm_tendency_static(const agcm_grid_t* g, int precision, const v
   return precision == AGCM_FP64 ? tendency_static<double>(g, (char*)base, U, V, Phi, pi, tU, tV, tPhi, tpi, st)
                                 : tendency_static<float>(g, (char*)base, U, V, Phi, pi, tU, tV, tPhi, tpi, st);
 }
+
+// ================================================================ ensembles
+struct agcm_ensemble {
+  int prec = AGCM_FP32;
+  std::vector<agcm_state*> members;
+  std::vector<char> host_desc;   // EnsMember<T>[n]
+  void* d_desc = nullptr;
+  agcm::EnsSync* d_sync = nullptr;
+  int queue_cap = 0;             // steps per launch
+  int nitems = 0;
+  int warps_per_block = 4;
+  int blocks_per_sm = 0;         // 0: as many as fit
+  double timeout_s = 1.0;
+  int test_missing = 0;
+  bool desc_dirty = true;
+  std::vector<double> last_dt;
+  Profiler prof;
+};
+
+namespace {
+
+template <class T>
+void fill_desc(agcm_ensemble* e) {
+  e->host_desc.assign(e->members.size() * sizeof(agcm::EnsMember<T>), 0);
+  auto* d = reinterpret_cast<agcm::EnsMember<T>*>(e->host_desc.data());
+  int begin = 0;
+  for (size_t m = 0; m < e->members.size(); ++m) {
+    agcm_state* s = e->members[m];
+    d[m].g = geom_of<T>(s);
+    for (int c = 0; c < 3; ++c) {
+      for (int f = 0; f < 4; ++f) d[m].x[c][f] = (T*)s->x[c][f];
+      d[m].ubar[c] = s->ubar[c];
+      d[m].vbar[c] = s->vbar[c];
+    }
+    d[m].nbx = (s->grid->I + 31) / 32;
+    d[m].item_begin = begin;
+    d[m].dt = (T)0;
+    begin += d[m].nbx * s->grid->J;
+  }
+  e->nitems = begin;
+}
+
+template <class T>
+int ensemble_step(agcm_ensemble* e, int nsteps, const double* dt, cudaStream_t st) {
+  auto* d = reinterpret_cast<agcm::EnsMember<T>*>(e->host_desc.data());
+  const size_t n = e->members.size();
+  bool changed = e->desc_dirty;
+  for (size_t m = 0; m < n; ++m)
+    if (e->last_dt.size() != n || e->last_dt[m] != dt[m]) changed = true;
+  if (changed) {
+    e->last_dt.assign(dt, dt + n);
+    for (size_t m = 0; m < n; ++m) d[m].dt = (T)dt[m];
+    CUDA_TRY(cudaMemcpyAsync(e->d_desc, e->host_desc.data(), e->host_desc.size(), cudaMemcpyHostToDevice, st));
+    e->desc_dirty = false;
+  }
+  for (agcm_state* s : e->members) {
+    int rc = ensure_bar<T>(s, st);
+    if (rc) return rc;
+  }
+  if (nsteps == 0) return AGCM_OK;  // prepared: dt uploaded, vertical means valid
+  int dev = 0, nsm = 0, clock_khz = 0, occ = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  CUDA_TRY(cudaDeviceGetAttribute(&clock_khz, cudaDevAttrClockRate, dev));
+  const int threads = 32 * e->warps_per_block;
+  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, agcm::k_ensemble<T>, threads, 0));
+  if (occ < 1) return fail(AGCM_EINVAL, "ensemble kernel does not fit with %d threads per block", threads);
+  const int per_sm = e->blocks_per_sm > 0 ? std::min(e->blocks_per_sm, occ) : occ;
+  const unsigned grid = (unsigned)(per_sm * nsm);
+  const long long limit = (long long)(e->timeout_s * (double)clock_khz * 1000.0);
+  const size_t sync_bytes = sizeof(agcm::EnsSync) + sizeof(unsigned) * (size_t)e->queue_cap * 3;
+  for (int done = 0; done < nsteps; done += e->queue_cap) {
+    const int chunk = std::min(e->queue_cap, nsteps - done);
+    CUDA_TRY(cudaMemsetAsync(e->d_sync, 0, sync_bytes, st));
+    e->prof.begin(KID_ENSEMBLE, st);
+    agcm::k_ensemble<T><<<grid, threads, 0, st>>>((const agcm::EnsMember<T>*)e->d_desc, (int)n, e->nitems, chunk,
+                                                  e->d_sync, grid + (unsigned)e->test_missing, limit);
+    e->prof.end(st);
+    CUDA_TRY(cudaGetLastError());
+  }
+  for (agcm_state* s : e->members) s->bar_valid = true;
+  return AGCM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int agcm_ensemble_create(agcm_state_t* const* members, int n, agcm_ensemble_t** out) {
+  if (!members || n < 1 || !out) return fail(AGCM_EINVAL, "need n >= 1 members and an output pointer");
+  *out = nullptr;
+  agcm_ensemble* e = new agcm_ensemble;
+  e->prec = members[0]->prec;
+  for (int m = 0; m < n; ++m) {
+    if (!members[m] || members[m]->prec != e->prec) {
+      delete e;
+      return fail(AGCM_EINVAL, "member %d is null or has another precision", m);
+    }
+    for (int q = 0; q < m; ++q)
+      if (members[q] == members[m]) {
+        delete e;
+        return fail(AGCM_EINVAL, "member %d appears twice", m);
+      }
+    e->members.push_back(members[m]);
+  }
+  if (e->prec == AGCM_FP64)
+    fill_desc<double>(e);
+  else
+    fill_desc<float>(e);
+  e->queue_cap = 1024;
+  e->d_desc = dev_alloc(e->host_desc.size());
+  e->d_sync = (agcm::EnsSync*)dev_alloc(sizeof(agcm::EnsSync) + sizeof(unsigned) * (size_t)e->queue_cap * 3);
+  if (!e->d_desc || !e->d_sync) {
+    dev_free(e->d_desc);
+    dev_free(e->d_sync);
+    delete e;
+    return fail(AGCM_ENOMEM, "device allocation for the ensemble failed");
+  }
+  for (agcm_state* s : e->members) const_cast<agcm_grid*>(s->grid)->refs++;
+  *out = e;
+  return AGCM_OK;
+}
+
+int agcm_ensemble_destroy(agcm_ensemble_t* e) {
+  if (!e) return AGCM_OK;
+  cudaDeviceSynchronize();
+  dev_free(e->d_desc);
+  dev_free(e->d_sync);
+  for (agcm_state* s : e->members) const_cast<agcm_grid*>(s->grid)->refs--;
+  delete e;
+  return AGCM_OK;
+}
+
+int agcm_ensemble_configure(agcm_ensemble_t* e, int warps_per_block, int blocks_per_sm) {
+  if (!e || warps_per_block < 1 || warps_per_block > 4 || blocks_per_sm < 0)
+    return fail(AGCM_EINVAL, "warps_per_block must be 1..4 and blocks_per_sm >= 0");
+  e->warps_per_block = warps_per_block;
+  e->blocks_per_sm = blocks_per_sm;
+  return AGCM_OK;
+}
+
+int agcm_ensemble_set_timeout(agcm_ensemble_t* e, double seconds, int test_missing_blocks) {
+  if (!e || !(seconds > 0.0) || seconds > 60.0 || test_missing_blocks < 0)
+    return fail(AGCM_EINVAL, "timeout must be in (0, 60] s and test_missing_blocks >= 0");
+  e->timeout_s = seconds;
+  e->test_missing = test_missing_blocks;
+  return AGCM_OK;
+}
+
+int agcm_ensemble_step(agcm_ensemble_t* e, int nsteps, const double* dt, void* stream) {
+  if (!e || nsteps < 0 || !dt) return fail(AGCM_EINVAL, "bad argument");
+  for (size_t m = 0; m < e->members.size(); ++m)
+    if (!std::isfinite(dt[m])) return fail(AGCM_EINVAL, "dt[%zu] is not finite", m);
+  cudaStream_t st = as_stream(stream);
+  return e->prec == AGCM_FP64 ? ensemble_step<double>(e, nsteps, dt, st) : ensemble_step<float>(e, nsteps, dt, st);
+}
+
+int agcm_ensemble_status(agcm_ensemble_t* e, void* stream) {
+  if (!e) return fail(AGCM_EINVAL, "null ensemble");
+  int status = 0;
+  cudaStream_t st = as_stream(stream);
+  CUDA_TRY(cudaMemcpyAsync(&status, &e->d_sync->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  if (status == AGCM_ETIMEOUT)
+    return fail(AGCM_ETIMEOUT, "a grid barrier of the ensemble kernel gave up waiting (not all blocks resident?)");
+  return AGCM_OK;
+}
+
+int agcm_ensemble_profile(agcm_ensemble_t* e, int enable, double* ms_total, int64_t* launches) {
+  if (!e) return fail(AGCM_EINVAL, "null ensemble");
+  if (ms_total && launches) {
+    if (e->prof.drain()) return fail(AGCM_ECUDA, "event synchronisation failed");
+    *ms_total = e->prof.ms[KID_ENSEMBLE];
+    *launches = e->prof.n[KID_ENSEMBLE];
+  }
+  if (enable >= 0) {
+    e->prof.reset();
+    e->prof.on = enable != 0;
+  }
+  return AGCM_OK;
+}
+
+}  // extern "C"

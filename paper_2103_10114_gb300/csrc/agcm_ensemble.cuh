@@ -1,0 +1,120 @@
+// agcm_ensemble.cuh — many members of uneven resolution in one persistent launch.
+//
+// Each member is a state on its own grid.  A work item is one row segment of
+// 32 columns of one member; each warp pulls items from a per-(step, stage)
+// device counter and runs the same column body as the single-state stage
+// kernel (fused_column), so a member advanced in an ensemble does the same
+// arithmetic as alone (bit-identical in FP32 on GB300; in FP64 the compiler
+// may contract multiply-adds differently in the two kernels, a few ulp).  Stages are separated by a grid-wide barrier whose
+// wait is bounded in time: if it runs out, the kernel records AGCM_ETIMEOUT in
+// the status word and every block returns; nothing spins forever and nothing
+// traps.  The launch is sized so that every block is resident at once.
+#pragma once
+#include "agcm_common.cuh"
+#include "agcm_fused.cuh"
+
+namespace agcm {
+
+template <class T>
+struct EnsMember {
+  Geom<T> g;
+  T* x[3][4];         // x_n, x_1, x_2: U, V, Phi, pi
+  double* ubar[3];    // FP64 vertical means of x[c]
+  double* vbar[3];
+  T dt;
+  int nbx;            // 32-column blocks per row
+  int item_begin;     // first global item of this member
+};
+
+struct EnsSync {
+  unsigned int count;       // barrier arrivals
+  unsigned int gen;         // barrier generation
+  int status;               // 0 or AGCM_ETIMEOUT (4)
+  int pad;
+  unsigned int queue[1];    // nsteps*3 item counters (flexible)
+};
+
+// Grid barrier with a bounded wait.  `expected` blocks must arrive; the wait
+// gives up after `limit` clock cycles and records the timeout.
+__device__ __forceinline__ bool ens_barrier(EnsSync* sy, unsigned expected, long long limit) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* vgen = &sy->gen;
+    volatile int* vst = &sy->status;
+    const unsigned int g0 = *vgen;
+    __threadfence();
+    const unsigned int arrived = atomicAdd(&sy->count, 1u) + 1u;
+    if (arrived == expected) {
+      sy->count = 0u;
+      __threadfence();
+      atomicAdd(&sy->gen, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*vgen == g0 && *vst == 0) {
+        if (clock64() - t0 > limit) {
+          atomicExch(&sy->status, 4);
+          break;
+        }
+        __nanosleep(256);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return *((volatile int*)&sy->status) == 0;
+}
+
+template <class T>
+__device__ __forceinline__ int ens_member_of(const EnsMember<T>* mem, int nmem, int item) {
+  int lo = 0, hi = nmem - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (mem[mid].item_begin <= item)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+template <class T>
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2)
+    k_ensemble(const EnsMember<T>* __restrict__ mem, int nmem, int nitems, int nsteps, EnsSync* sy,
+               unsigned expected_blocks, long long limit) {
+  const int lane = threadIdx.x & 31;
+  for (int step = 0; step < nsteps; ++step) {
+    for (int stage = 0; stage < 3; ++stage) {
+      unsigned int* q = &sy->queue[step * 3 + stage];
+      while (true) {
+        int item = 0;
+        if (lane == 0) item = (int)atomicAdd(q, 1u);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= nitems) break;
+        const int m = ens_member_of(mem, nmem, item);
+        const EnsMember<T>& e = mem[m];
+        const int local = item - e.item_begin;
+        const int j = local / e.nbx;
+        const int i = (local - j * e.nbx) * 32 + lane;
+        if (i < e.g.I) {
+          const Geom<T>& g = e.g;
+          if (stage == 0) {
+            fused_column<T, 1>(g, i, j, e.x[0][0], e.x[0][1], e.x[0][2], e.x[0][3], e.ubar[0], e.vbar[0], nullptr,
+                               nullptr, nullptr, nullptr, e.x[1][0], e.x[1][1], e.x[1][2], e.x[1][3], e.ubar[1],
+                               e.vbar[1], T(0.5) * e.dt);
+          } else {
+            // stage 2: x1 -> x2; stage 3: x2 -> x_n in place; base x_n in both
+            const int a = stage, b = stage == 1 ? 2 : 0;
+            const T c = stage == 1 ? T(0.5) * e.dt : e.dt;
+            fused_column<T, 2>(g, i, j, e.x[a][0], e.x[a][1], e.x[a][2], e.x[a][3], e.ubar[a], e.vbar[a],
+                               e.x[0][0], e.x[0][1], e.x[0][2], e.x[0][3], e.x[b][0], e.x[b][1], e.x[b][2],
+                               e.x[b][3], e.ubar[b], e.vbar[b], c);
+          }
+        }
+      }
+      __threadfence();
+      if (!ens_barrier(sy, expected_blocks, limit)) return;
+    }
+  }
+}
+
+}  // namespace agcm

@@ -44,19 +44,16 @@ namespace agcm {
 #endif
 constexpr int kFusedBX = 32, kFusedBY = AGCM_FUSED_BY;
 
+// The work of one thread: the column (j, i) through all levels of one stage.
 // MODE 0: out = T(xs) (validation); MODE 1: base = xs (first stage);
 // MODE 2: base given (later stages; may alias out).
 template <class T, int MODE>
-__global__ void __launch_bounds__(kFusedBX * kFusedBY, sizeof(T) == 4 ? AGCM_FUSED_MINB : AGCM_FUSED_MINB64)
-    k_fused_stage(
-    Geom<T> g, const T* __restrict__ U, const T* __restrict__ V, const T* __restrict__ Phi,
-    const T* __restrict__ pi, const double* __restrict__ Ubar, const double* __restrict__ Vbar, const T* Ub,
-    const T* Vb, const T* Phib, const T* pib, T* Uo, T* Vo, T* Phio, T* pio, double* __restrict__ Ubar_o,
-    double* __restrict__ Vbar_o, T cdt) {
+__device__ __forceinline__ void fused_column(
+    const Geom<T>& g, const int i, const int j, const T* __restrict__ U, const T* __restrict__ V,
+    const T* __restrict__ Phi, const T* __restrict__ pi, const double* __restrict__ Ubar,
+    const double* __restrict__ Vbar, const T* Ub, const T* Vb, const T* Phib, const T* pib, T* Uo, T* Vo, T* Phio,
+    T* pio, double* __restrict__ Ubar_o, double* __restrict__ Vbar_o, const T cdt) {
   const int I = g.I, J = g.J, K = g.K;
-  const int i = blockIdx.x * kFusedBX + threadIdx.x;
-  const int j = kFusedBY == 1 ? (int)blockIdx.y : (int)(blockIdx.y * kFusedBY + threadIdx.y);
-  if (i >= I || j >= J) return;
   const bool hasS = j < J - 1;   // V row j exists, scalar row j+1 exists
   const bool hasN = j > 0;       // V row j-1 exists
   const bool hasSS = j + 1 < J - 1;  // V row j+1 exists
@@ -290,6 +287,19 @@ __global__ void __launch_bounds__(kFusedBX * kFusedBY, sizeof(T) == 4 ? AGCM_FUS
     Ubar_o[rj + i] = ubar;
     if (hasS) Vbar_o[rj + i] = vbar;
   }
+}
+
+template <class T, int MODE>
+__global__ void __launch_bounds__(kFusedBX * kFusedBY, sizeof(T) == 4 ? AGCM_FUSED_MINB : AGCM_FUSED_MINB64)
+    k_fused_stage(Geom<T> g, const T* __restrict__ U, const T* __restrict__ V, const T* __restrict__ Phi,
+                  const T* __restrict__ pi, const double* __restrict__ Ubar, const double* __restrict__ Vbar,
+                  const T* Ub, const T* Vb, const T* Phib, const T* pib, T* Uo, T* Vo, T* Phio, T* pio,
+                  double* __restrict__ Ubar_o, double* __restrict__ Vbar_o, T cdt) {
+  const int i = blockIdx.x * kFusedBX + threadIdx.x;
+  const int j = kFusedBY == 1 ? (int)blockIdx.y : (int)(blockIdx.y * kFusedBY + threadIdx.y);
+  if (i >= g.I || j >= g.J) return;
+  fused_column<T, MODE>(g, i, j, U, V, Phi, pi, Ubar, Vbar, Ub, Vb, Phib, pib, Uo, Vo, Phio, pio, Ubar_o, Vbar_o,
+                        cdt);
 }
 
 // Vertical means Ubar = sum_k dsigma_k U_k, Vbar likewise (FP64), of a state.

@@ -1,0 +1,122 @@
+"""Ensembles of members of uneven resolution: one persistent launch per call,
+an autotuner for its launch shape, and CUDA-graph replay.
+
+The launch shape (warps per block, blocks per SM) decides how the work items
+(32-column row segments of every member) are spread over the SMs; the best
+shape depends on the member mix and the GPU, so `autotune` times each
+candidate on the ensemble itself and keeps the fastest (cached per member mix
+and device name for the life of the process).
+"""
+from __future__ import annotations
+
+import ctypes
+
+from . import agcm
+
+_TUNE_CACHE: dict = {}
+
+
+class Ensemble:
+    def __init__(self, states):
+        self.states = list(states)
+        arr = (ctypes.c_void_p * len(self.states))(*[s.handle for s in self.states])
+        h = ctypes.c_void_p()
+        agcm.check(agcm.lib().agcm_ensemble_create(arr, len(self.states), ctypes.byref(h)))
+        self._h = h
+        self.shape = (4, 0)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def points(self):
+        return sum(s.grid.points() for s in self.states)
+
+    def configure(self, warps_per_block, blocks_per_sm):
+        agcm.check(agcm.lib().agcm_ensemble_configure(self._h, int(warps_per_block), int(blocks_per_sm)))
+        self.shape = (int(warps_per_block), int(blocks_per_sm))
+
+    def set_timeout(self, seconds, test_missing_blocks=0):
+        agcm.check(agcm.lib().agcm_ensemble_set_timeout(self._h, float(seconds), int(test_missing_blocks)))
+
+    def step(self, nsteps, dts, stream=None):
+        arr = (ctypes.c_double * len(self.states))(*[float(d) for d in dts])
+        agcm.check(agcm.lib().agcm_ensemble_step(self._h, int(nsteps), arr, agcm._stream_ptr(stream)))
+
+    def status(self, stream=None):
+        """Synchronises; raises AgcmError(AGCM_ETIMEOUT) if a barrier gave up."""
+        agcm.check(agcm.lib().agcm_ensemble_status(self._h, agcm._stream_ptr(stream)))
+
+    def profile(self, enable=True):
+        agcm.check(agcm.lib().agcm_ensemble_profile(self._h, 1 if enable else 0, None, None))
+
+    def profile_read(self):
+        ms, n = ctypes.c_double(), ctypes.c_int64()
+        agcm.check(agcm.lib().agcm_ensemble_profile(self._h, -1, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
+
+    def signature(self):
+        import torch
+
+        return (torch.cuda.get_device_name(), tuple((s.grid.nlon, s.grid.nlat, s.grid.nlev, s.precision)
+                                                    for s in self.states))
+
+    def autotune(self, dts, steps=2, candidates=None, verbose=False):
+        """Time each launch shape on this ensemble (the states are restored
+        afterwards) and keep the fastest.  Returns (shape, {shape: ms/step})."""
+        import torch
+
+        key = self.signature()
+        if key in _TUNE_CACHE:
+            self.configure(*_TUNE_CACHE[key])
+            return _TUNE_CACHE[key], {}
+        if candidates is None:
+            candidates = [(w, b) for w in (1, 2, 4) for b in (0, 2, 4, 8) if not (w == 1 and b in (2, 4))]
+        saved = [s.store() for s in self.states]
+        times = {}
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for shape in candidates:
+            self.configure(*shape)
+            self.step(1, dts)
+            torch.cuda.synchronize()
+            e0.record()
+            self.step(steps, dts)
+            e1.record()
+            torch.cuda.synchronize()
+            self.status()
+            times[shape] = e0.elapsed_time(e1) / steps
+            if verbose:
+                print("ensemble shape", shape, f"{times[shape]:.3f} ms/step")
+        best = min(times, key=times.get)
+        for s, x in zip(self.states, saved):
+            s.load(x)
+        self.configure(*best)
+        _TUNE_CACHE[key] = best
+        return best, times
+
+    def capture(self, nsteps, dts):
+        """A CUDA graph of `nsteps` ensemble steps (one persistent launch);
+        replay it with graph.replay()."""
+        import torch
+
+        self.step(0, dts)  # uploads dt and the vertical means outside the capture
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                self.step(nsteps, dts, stream=s)
+        torch.cuda.current_stream().wait_stream(s)
+        return g
+
+    def close(self):
+        if getattr(self, "_h", None):
+            agcm.check(agcm.lib().agcm_ensemble_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

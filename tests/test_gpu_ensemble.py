@@ -1,0 +1,119 @@
+"""Ensemble persistent kernel: member k equals its own single-state run, graph
+replay equals eager launches, the bounded barrier reports a timeout without
+hanging, and the autotuner picks a valid shape."""
+import numpy as np
+import pytest
+
+from paper_2103_10114_gb300 import agcm, inputs
+from paper_2103_10114_gb300.ensemble import Ensemble
+
+pytestmark = pytest.mark.gpu
+FIELDS = agcm.FIELDS
+MIX = [(64, 32, 6), (48, 24, 5), (37, 23, 4), (96, 48, 8)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built(cuda_ok):
+    agcm.build()
+    agcm.lib()
+
+
+def members(prec, mix=MIX, seed0=100):
+    out = []
+    for n, (I, J, K) in enumerate(mix):
+        st = inputs.baroclinic_jet(I, J, K, seed=seed0 + n, noise=1e-2, terrain_seed=2)
+        g = agcm.Grid(I, J, K, phis=st["phis"])
+        s = agcm.State(g, prec)
+        s.load(st)
+        out.append((g, s, st, g.dt(100.0)))
+    return out
+
+
+def np_state(s):
+    return {f: v.double().cpu().numpy() for f, v in s.store().items()}
+
+
+@pytest.mark.parametrize("prec", [agcm.AGCM_FP32, agcm.AGCM_FP64])
+def test_member_equals_single_run(prec):
+    mem = members(prec)
+    ens = Ensemble([m[1] for m in mem])
+    dts = [m[3] for m in mem]
+    ens.step(3, dts)
+    ens.status()
+    for g, s, st, dt in mem:
+        got = np_state(s)
+        alone = agcm.State(g, prec)
+        alone.load(st)
+        alone.step(3, dt)
+        want = np_state(alone)
+        for f in FIELDS:
+            if prec == agcm.AGCM_FP32:  # same kernel body: identical bits
+                assert np.array_equal(got[f], want[f]), (g.nlon, f, np.abs(got[f] - want[f]).max())
+            else:  # FP64: the compiler may fuse multiply-adds differently in the two kernels
+                err = np.abs(got[f] - want[f]).max() / np.abs(want[f]).max()
+                assert err <= 1e-13, (g.nlon, f, err)
+    ens.close()
+
+
+def test_graph_replay_equals_eager():
+    import torch
+
+    mem = members(agcm.AGCM_FP32)
+    ens = Ensemble([m[1] for m in mem])
+    dts = [m[3] for m in mem]
+    x0 = [m[1].store() for m in mem]
+    graph = ens.capture(2, dts)
+    graph.replay()
+    graph.replay()
+    torch.cuda.synchronize()
+    ens.status()
+    replayed = [np_state(m[1]) for m in mem]
+    for (g, s, st, dt), x in zip(mem, x0):
+        s.load(x)
+    ens.step(4, dts)
+    ens.status()
+    for m, r in zip(mem, replayed):
+        e = np_state(m[1])
+        for f in FIELDS:
+            assert np.array_equal(e[f], r[f])
+    ens.close()
+
+
+def test_barrier_timeout_is_reported_and_context_survives():
+    mem = members(agcm.AGCM_FP32, mix=[(64, 32, 6), (48, 24, 5)])
+    ens = Ensemble([m[1] for m in mem])
+    dts = [m[3] for m in mem]
+    x0 = [m[1].store() for m in mem]
+    ens.set_timeout(0.2, test_missing_blocks=1)  # every barrier waits for a block that never comes
+    ens.step(1, dts)
+    with pytest.raises(agcm.AgcmError) as e:
+        ens.status()
+    assert e.value.code == agcm.AGCM_ETIMEOUT
+    # the context is still usable: a normal run afterwards is correct
+    ens.set_timeout(1.0, 0)
+    for m, x in zip(mem, x0):
+        m[1].load(x)
+    ens.step(2, dts)
+    ens.status()
+    for g, s, st, dt in mem:
+        alone = agcm.State(g, agcm.AGCM_FP32)
+        alone.load(st)
+        alone.step(2, dt)
+        a, b = np_state(s), np_state(alone)
+        for f in FIELDS:
+            assert np.array_equal(a[f], b[f])
+    ens.close()
+
+
+def test_autotune_picks_a_shape_and_keeps_state():
+    mem = members(agcm.AGCM_FP32)
+    ens = Ensemble([m[1] for m in mem])
+    dts = [m[3] for m in mem]
+    before = [np_state(m[1]) for m in mem]
+    shape, times = ens.autotune(dts, steps=1)
+    assert shape in times and all(t > 0 for t in times.values())
+    after = [np_state(m[1]) for m in mem]
+    for a, b in zip(before, after):
+        for f in FIELDS:
+            assert np.array_equal(a[f], b[f])
+    ens.close()

@@ -28,6 +28,20 @@ sys.path.insert(0, ROOT)
 WORKLOAD = (1440, 720, 30)
 BYTES_PER_POINT_STEP = {4: 96, 8: 192}  # 24 words: stages read/write 6 + 9 + 9 words
 
+# DRAM traffic of the dominant kernel from an ncu capture of this workload
+# (profiles/), valid only while the kernel source is the one that was captured.
+NCU_TRAFFIC = {
+    # kernel name: (sha1 of csrc/agcm_fused.cuh at capture time, bytes per launch, profile file)
+}
+
+
+def kernel_source_hash():
+    import hashlib
+
+    p = os.path.join(ROOT, "paper_2103_10114_gb300", "csrc", "agcm_fused.cuh")
+    with open(p, "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()
+
 
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -101,12 +115,13 @@ def dist_setup():
     return 0, 1, 0
 
 
-def cpu_oracle_rate(nlon, nlat, nlev, steps=1):
+def cpu_oracle_rate(nlon, nlat, nlev, steps=1, st=None):
     """Time the FP64 oracle on one grid; returns (gp-steps/s, seconds)."""
     import oracle
     from paper_2103_10114_gb300 import inputs
 
-    st = inputs.baroclinic_jet(nlon, nlat, nlev, seed=5, noise=1e-2, terrain_seed=2)
+    if st is None:
+        st = inputs.baroclinic_jet(nlon, nlat, nlev, seed=5, noise=1e-2, terrain_seed=2)
     o = oracle.Oracle(nlon, nlat, nlev, phis=st["phis"])
     dt = 60.0
     t0 = time.perf_counter()
@@ -143,7 +158,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -226,6 +241,10 @@ def main():
     name, (kms, kn) = max(prof.items(), key=lambda kv: kv[1][0])
     stage_bytes = pts * 8 * esz
     achieved = stage_bytes / (kms / kn / 1e3) / 1e9 if name in ("k_update", "k_fused_stage") else None
+    traffic, traffic_src = None, None
+    rec = NCU_TRAFFIC.get(name)
+    if rec and rec[0] == kernel_source_hash():
+        traffic, traffic_src = rec[1], rec[2]
     launches = sum(n for _, n in prof.values())
     line = {
         "metric": "grid-point-steps/s", "value": value, "unit": "gp-steps/s", "n_gpus": world,
@@ -236,8 +255,9 @@ def main():
                    "l2": "inputs larger than L2 (state 373 MB)"},
         "hbm_frac_step": value / world * BYTES_PER_POINT_STEP[esz] / (peak * 1e9),
         "roofline": {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": None, "peak_kind": peak_kind,
-                     "bytes_per_launch": stage_bytes, "avg_launch_ms": kms / kn},
+                     "frac": (achieved / peak) if achieved else None, "traffic": traffic, "peak_kind": peak_kind,
+                     "traffic_source": traffic_src, "bytes_per_launch": stage_bytes, "avg_launch_ms": kms / kn,
+                     "note": "peak = measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},
         "kernels": {k: {"ms_total": v[0], "launches": v[1], "share": v[0] / sum(x[0] for x in prof.values())}
                     for k, v in prof.items()},
         "e2e": {"value": e2e, "unit": "gp-steps/s", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
@@ -249,17 +269,31 @@ def main():
     if rank == 0 and not args.no_forms:
         line["forms"] = measure_forms(agcm, inputs, torch)
     if rank == 0 and not args.no_cpu_baseline:
-        rate, el = cpu_oracle_rate(720, 360, 30)
+        rate, el = cpu_oracle_rate(I, J, K, st=st)
         line["cpu_baseline"] = {"value": rate, "unit": "gp-steps/s", "cores": 1, "kind": "oracle",
-                                "sample": f"one FP64 oracle step of the same model on 720x360x30 ({el:.1f} s)"}
+                                "sample": f"one FP64 oracle step of the full {I}x{J}x{K} workload ({el:.1f} s)"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
 
 
+def _time(torch, fn, reps):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
 def measure_forms(agcm, inputs, torch, steps=5):
-    """gp-steps/s of the other forms on the same GPU (FP64 plain at the same size)."""
+    """gp-steps/s of the other forms on the same GPU: plain FP64 at the same size,
+    FP32 at 256x128x30, the 64-member ensemble (one persistent launch, autotuned,
+    replayed from a CUDA graph) against per-member FP64 launches, and the
+    adjoint step at 720x360x30."""
     out = {}
     I, J, K = WORKLOAD
     st = inputs.baroclinic_jet(I, J, K, seed=6, noise=1e-2, terrain_seed=2)
@@ -268,16 +302,110 @@ def measure_forms(agcm, inputs, torch, steps=5):
     s = agcm.State(g, agcm.AGCM_FP64)
     s.load(st)
     s.step(2, dt)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    s.step(steps, dt)
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    out["fp64_1440x720x30"] = {"value": I * J * K * steps / (ms / 1e3), "unit": "gp-steps/s", "ms_per_step": ms / steps}
+    ms = _time(torch, lambda: s.step(steps, dt), 1) / steps
+    out["fp64_1440x720x30"] = {"value": I * J * K / (ms / 1e3), "unit": "gp-steps/s", "ms_per_step": ms,
+                               "bound": "fp64 pipe (GB300 runs FP64 at 2 lanes/SM/cycle)"}
     s.close()
+    # FP32 at the precision-comparison size (state fits in L2)
+    I2, J2, K2 = 256, 128, 30
+    st2 = inputs.baroclinic_jet(I2, J2, K2, seed=3, terrain_seed=2)
+    g2 = agcm.Grid(I2, J2, K2, phis=st2["phis"])
+    for prec, tag in ((agcm.AGCM_FP32, "fp32"), (agcm.AGCM_FP64, "fp64")):
+        s2 = agcm.State(g2, prec)
+        s2.load(st2)
+        s2.step(3, g2.dt(100.0))
+        ms = _time(torch, lambda: s2.step(20, g2.dt(100.0)), 1) / 20
+        out[f"{tag}_256x128x30"] = {"value": I2 * J2 * K2 / (ms / 1e3), "unit": "gp-steps/s", "ms_per_step": ms,
+                                    "note": "state fits in L2"}
+        s2.close()
+    try:
+        out["ensemble_64"] = measure_ensemble(agcm, inputs, torch)
+    except Exception as e:  # reported, not hidden
+        out["ensemble_64"] = {"error": repr(e)}
+    try:
+        out["adjoint_720x360x30"] = measure_adjoint(agcm, inputs, torch)
+    except Exception as e:
+        out["adjoint_720x360x30"] = {"error": repr(e)}
     return out
+
+
+def measure_ensemble(agcm, inputs, torch, steps=10):
+    """Config 4: 32 @ 256x128x30 + 24 @ 360x180x30 + 8 @ 720x360x30, FP32,
+    one persistent launch per call, autotuned and replayed from a CUDA graph;
+    against 64 per-member launches of the plain FP64 step."""
+    from paper_2103_10114_gb300.ensemble import Ensemble
+
+    terr = {}
+    states, grids, dts = [], [], []
+    for (I, J, K), seed, noise in inputs.ensemble_members():
+        if (I, J) not in terr:
+            terr[(I, J)] = inputs.terrain_phis(I, J, seed=2)
+        st = inputs.baroclinic_jet(I, J, K, seed=seed, noise=noise, terrain_seed=None)
+        st["phis"] = terr[(I, J)]
+        g = agcm.Grid(I, J, K, phis=st["phis"])
+        s = agcm.State(g, agcm.AGCM_FP32)
+        s.load(st)
+        grids.append((g, st))
+        states.append(s)
+        dts.append(g.dt(100.0))
+    pts = sum(g.points() for g, _ in grids)
+    ens = Ensemble(states)
+    shape, times = ens.autotune(dts, steps=2)
+    graph = ens.capture(steps, dts)
+    graph.replay()
+    ens.profile(True)
+    ms = _time(torch, graph.replay, 1) / steps
+    kms, kn = ens.profile_read()
+    ens.profile(False)
+    ens.status()
+    res = {"value": pts / (ms / 1e3), "unit": "gp-steps/s", "ms_per_step": ms, "points": pts,
+           "shape": list(shape), "tuned_ms": {f"{w}x{b}": round(t, 4) for (w, b), t in times.items()},
+           "hbm_frac_step": pts / (ms / 1e3) * 96 / (peaks()[0] * 1e9)}
+    ens.close()
+    for s in states:
+        s.close()
+    # per-member launches of the plain FP64 step
+    s64 = []
+    for (g, st) in grids:
+        s = agcm.State(g, agcm.AGCM_FP64)
+        s.load(st)
+        s64.append(s)
+    for s, d in zip(s64, dts):
+        s.step(1, d)
+
+    def one():
+        for s, d in zip(s64, dts):
+            s.step(1, d)
+
+    ms64 = _time(torch, one, 3)
+    res["per_member_fp64"] = {"value": pts / (ms64 / 1e3), "unit": "gp-steps/s", "ms_per_step": ms64,
+                              "launches_per_step": 3 * len(s64)}
+    res["speedup_vs_per_member_fp64"] = ms64 / ms
+    for s in s64:
+        s.close()
+    return res
+
+
+def measure_adjoint(agcm, inputs, torch, steps=5):
+    """Config 3 grid 720x360x30: adjoint steps per second (each recomputes its
+    two stage states) in FP32 and FP64."""
+    I, J, K = 720, 360, 30
+    st = inputs.baroclinic_jet(I, J, K, seed=3, noise=1e-2, terrain_seed=2)
+    g = agcm.Grid(I, J, K, phis=st["phis"])
+    dt = g.dt(100.0)
+    res = {}
+    for prec, tag in ((agcm.AGCM_FP32, "fp32"), (agcm.AGCM_FP64, "fp64")):
+        s = agcm.State(g, prec)
+        s.load(st)
+        lam = s.store()
+        s.step_adjoint(lam, dt)
+        ms = _time(torch, lambda: s.step_adjoint(lam, dt), steps)
+        s.step(1, dt)
+        fms = _time(torch, lambda: s.step(1, dt), steps)
+        res[tag] = {"value": I * J * K / (ms / 1e3), "unit": "gp-steps/s", "ms_per_adjoint_step": ms,
+                    "ms_per_forward_step": fms, "adjoint_over_forward": ms / fms}
+        s.close()
+    return res
 
 
 if __name__ == "__main__":

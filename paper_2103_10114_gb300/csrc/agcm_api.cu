@@ -194,6 +194,7 @@ struct agcm_state {
   bool bar_valid = false;
   // diagnostics partials
   double* diag = nullptr;
+  int* err = nullptr;  // device status word: AGCM_ETIMEOUT if a bounded wait gave up
   std::vector<void*> owned;
   // adjoint workspace (allocated on the first agcm_step_adjoint call)
   bool adj_ready = false;
@@ -376,26 +377,62 @@ int ensure_bar(agcm_state* s, cudaStream_t st) {
 // One fused stage: out = base + cdt * T(x[in]) (MODE 1: base = x[in]; MODE 2:
 // base = x[0]; MODE 0: out = T).  Writes the vertical means of out to bar[outb]
 // (outb < 0: not written).
+// Launch of the stage kernel.  AGCM_STAGE_TILE selects the shape: 0 = one
+// warp per 32-column row segment with global loads (default: fastest on GB300
+// at 1440x720x30, see the design notes), 1 = 32 x 4 tiles staged by TMA.
+#ifndef AGCM_STAGE_TILE
+#define AGCM_STAGE_TILE 0
+#endif
 template <class T, int MODE>
-int fused_stage(agcm_state* s, int in, void* const out[4], int outb, double cdt, cudaStream_t st) {
-  const agcm::Geom<T>& G = geom_of<T>(s);
-  const dim3 block(agcm::kFusedBX, agcm::kFusedBY);
-  const dim3 grid((unsigned)((G.I + agcm::kFusedBX - 1) / agcm::kFusedBX),
-                  (unsigned)((G.J + agcm::kFusedBY - 1) / agcm::kFusedBY));
-  void* const* xs = s->x[in];
-  void* const* xb = s->x[0];
-  s->prof.begin(KID_FUSED, st);
-  agcm::k_fused_stage<T, MODE><<<grid, block, 0, st>>>(
-      G, (const T*)xs[0], (const T*)xs[1], (const T*)xs[2], (const T*)xs[3], s->ubar[in], s->vbar[in],
-      (const T*)xb[0], (const T*)xb[1], (const T*)xb[2], (const T*)xb[3], (T*)out[0], (T*)out[1], (T*)out[2],
-      (T*)out[3], outb >= 0 ? s->ubar[outb] : nullptr, outb >= 0 ? s->vbar[outb] : nullptr, (T)cdt);
-  s->prof.end(st);
+int launch_fused(const agcm::Geom<T>& G, const void* const xs[4], const double* ub, const double* vb,
+                 const void* const xb[4], void* const out[4], double* ubo, double* vbo, const double* ubb,
+                 const double* vbb, double cdt, int* err, cudaStream_t st) {
+  if (!AGCM_STAGE_TILE) {
+    const dim3 block(agcm::kTileX, 1);
+    const dim3 grid((unsigned)((G.I + agcm::kTileX - 1) / agcm::kTileX), (unsigned)G.J);
+    agcm::k_fused_stage<T, MODE, 1><<<grid, block, 0, st>>>(
+        G, (const T*)xs[0], (const T*)xs[1], (const T*)xs[2], (const T*)xs[3], ub, vb, (const T*)xb[0],
+        (const T*)xb[1], (const T*)xb[2], (const T*)xb[3], (T*)out[0], (T*)out[1], (T*)out[2], (T*)out[3], ubo, vbo,
+        ubb, vbb, (T)cdt, 0, err);
+    CUDA_TRY(cudaGetLastError());
+    return AGCM_OK;
+  }
+  static bool attr_set = false;  // per process; the attribute is per function
+  const size_t smem = agcm::tile_smem_bytes<T>();
+  if (!attr_set) {
+    CUDA_TRY(cudaFuncSetAttribute(agcm::k_fused_stage<T, MODE, agcm::kTileY>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr_set = true;
+  }
+  // the bulk copies need 16-byte aligned row segments of the stage input
+  int tile = 1;
+  for (int f = 0; f < 3; ++f)
+    if (((uintptr_t)xs[f]) & 15) tile = 0;
+  const dim3 block(agcm::kTileX, agcm::kTileY);
+  const dim3 grid((unsigned)((G.I + agcm::kTileX - 1) / agcm::kTileX),
+                  (unsigned)((G.J + agcm::kTileY - 1) / agcm::kTileY));
+  agcm::k_fused_stage<T, MODE, agcm::kTileY><<<grid, block, smem, st>>>(
+      G, (const T*)xs[0], (const T*)xs[1], (const T*)xs[2], (const T*)xs[3], ub, vb, (const T*)xb[0],
+      (const T*)xb[1], (const T*)xb[2], (const T*)xb[3], (T*)out[0], (T*)out[1], (T*)out[2], (T*)out[3], ubo, vbo,
+      ubb, vbb, (T)cdt, tile, err);
   CUDA_TRY(cudaGetLastError());
   return AGCM_OK;
 }
 
+template <class T, int MODE>
+int fused_stage(agcm_state* s, int in, void* const out[4], int outb, double cdt, cudaStream_t st) {
+  const agcm::Geom<T>& G = geom_of<T>(s);
+  s->prof.begin(KID_FUSED, st);
+  int rc = launch_fused<T, MODE>(G, s->x[in], s->ubar[in], s->vbar[in], s->x[0], out,
+                                 outb >= 0 ? s->ubar[outb] : nullptr, outb >= 0 ? s->vbar[outb] : nullptr,
+                                 s->ubar[0], s->vbar[0], cdt, s->err, st);
+  s->prof.end(st);
+  return rc;
+}
+
 template <class T>
 int run_steps(agcm_state* s, int nsteps, double dt, cudaStream_t st) {
+  if (sizeof(T) == 4) s->bar_valid = false;  // exact means once per call in FP32
   int rc = ensure_bar<T>(s, st);
   if (rc) return rc;
   for (int n = 0; n < nsteps; ++n) {
@@ -625,6 +662,8 @@ int agcm_state_create(const agcm_grid_t* g, int precision, int nmembers, agcm_st
     ok = ok && (s->vbar[c] = (double*)get(s->n2 * sizeof(double)));
   }
   ok = ok && (s->diag = (double*)get((agcm::kDiagPartials + 1) * 8 * sizeof(double)));
+  ok = ok && (s->err = (int*)get(256));
+  if (ok) cudaMemset(s->err, 0, sizeof(int));
   if (!ok) {
     for (void* p : s->owned) dev_free(p);
     delete s;
@@ -718,6 +757,9 @@ int agcm_diagnostics(const agcm_state_t* s, agcm_diag_t* out, void* stream) {
   out->max_v = h[5];
   out->finite = h[6] == 0.0 ? 1 : 0;
   out->reserved = 0;
+  int e = 0;
+  CUDA_TRY(cudaMemcpy(&e, s->err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e == AGCM_ETIMEOUT) return fail(AGCM_ETIMEOUT, "a bounded wait in the stage kernel gave up");
   if (!out->finite) return fail(AGCM_ENONFINITE, "state holds %g non-finite values", h[6]);
   return AGCM_OK;
 }
@@ -989,14 +1031,10 @@ int tendency_static(const agcm_grid* g, char* base, const void* U, const void* V
   double* ubar = (double*)(base + kOffBar);
   double* vbar = (double*)(base + kOffBar + kColB);
   agcm::k_vsum<T><<<nblocks((size_t)I * J, 256), 256, 0, st>>>(G, (const T*)U, (const T*)V, ubar, vbar);
-  const dim3 block(agcm::kFusedBX, agcm::kFusedBY);
-  const dim3 grid((unsigned)((I + agcm::kFusedBX - 1) / agcm::kFusedBX),
-                  (unsigned)((J + agcm::kFusedBY - 1) / agcm::kFusedBY));
-  agcm::k_fused_stage<T, 0><<<grid, block, 0, st>>>(G, (const T*)U, (const T*)V, (const T*)Phi, (const T*)pi, ubar,
-                                                    vbar, nullptr, nullptr, nullptr, nullptr, (T*)tU, (T*)tV,
-                                                    (T*)tPhi, (T*)tpi, nullptr, nullptr, (T)1);
-  CUDA_TRY(cudaGetLastError());
-  return AGCM_OK;
+  const void* xs[4] = {U, V, Phi, pi};
+  const void* none[4] = {nullptr, nullptr, nullptr, nullptr};
+  void* out[4] = {tU, tV, tPhi, tpi};
+  return launch_fused<T, 0>(G, xs, ubar, vbar, none, out, nullptr, nullptr, nullptr, nullptr, 1.0, nullptr, st);
 }
 
 }  // namespace
@@ -1089,6 +1127,7 @@ int ensemble_step(agcm_ensemble* e, int nsteps, const double* dt, cudaStream_t s
     e->desc_dirty = false;
   }
   for (agcm_state* s : e->members) {
+    if (sizeof(T) == 4 && nsteps > 0) s->bar_valid = false;  // exact means once per call in FP32
     int rc = ensure_bar<T>(s, st);
     if (rc) return rc;
   }

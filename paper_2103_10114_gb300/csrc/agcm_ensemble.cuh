@@ -98,16 +98,16 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2)
         if (i < e.g.I) {
           const Geom<T>& g = e.g;
           if (stage == 0) {
-            fused_column<T, 1>(g, i, j, e.x[0][0], e.x[0][1], e.x[0][2], e.x[0][3], e.ubar[0], e.vbar[0], nullptr,
-                               nullptr, nullptr, nullptr, e.x[1][0], e.x[1][1], e.x[1][2], e.x[1][3], e.ubar[1],
-                               e.vbar[1], T(0.5) * e.dt);
+            fused_column<T, 1, false>(g, i, j, e.x[0][0], e.x[0][1], e.x[0][2], e.x[0][3], e.ubar[0], e.vbar[0],
+                                      nullptr, nullptr, nullptr, nullptr, e.x[1][0], e.x[1][1], e.x[1][2],
+                                      e.x[1][3], e.ubar[1], e.vbar[1], e.ubar[0], e.vbar[0], T(0.5) * e.dt);
           } else {
             // stage 2: x1 -> x2; stage 3: x2 -> x_n in place; base x_n in both
             const int a = stage, b = stage == 1 ? 2 : 0;
             const T c = stage == 1 ? T(0.5) * e.dt : e.dt;
-            fused_column<T, 2>(g, i, j, e.x[a][0], e.x[a][1], e.x[a][2], e.x[a][3], e.ubar[a], e.vbar[a],
-                               e.x[0][0], e.x[0][1], e.x[0][2], e.x[0][3], e.x[b][0], e.x[b][1], e.x[b][2],
-                               e.x[b][3], e.ubar[b], e.vbar[b], c);
+            fused_column<T, 2, false>(g, i, j, e.x[a][0], e.x[a][1], e.x[a][2], e.x[a][3], e.ubar[a], e.vbar[a],
+                                      e.x[0][0], e.x[0][1], e.x[0][2], e.x[0][3], e.x[b][0], e.x[b][1], e.x[b][2],
+                                      e.x[b][3], e.ubar[b], e.vbar[b], e.ubar[0], e.vbar[0], c);
           }
         }
       }

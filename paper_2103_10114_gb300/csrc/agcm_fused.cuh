@@ -44,15 +44,125 @@ namespace agcm {
 #endif
 constexpr int kFusedBX = 32, kFusedBY = AGCM_FUSED_BY;
 
+// ---- shared-memory tile staged by the TMA bulk-copy engine
+constexpr int kTileX = 32, kTileY = 4;          // one block = 32 columns x 4 rows
+constexpr int kHaloMax = 64;                    // leap strides up to 63 are staged
+constexpr int kPitch = kTileX + 2 * kHaloMax;   // row pitch of a staged segment
+constexpr int kTileRows = kTileY + 2;           // rows j0-1 .. j0+4
+constexpr int kStages = 3;                      // levels in flight
+#ifndef AGCM_TILE_MINB
+#define AGCM_TILE_MINB 5
+#endif
+template <class T>
+constexpr size_t tile_smem_bytes() {
+  return 64 + sizeof(T) * (size_t)kStages * 3 * kTileRows * kPitch;
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: gives up after about a second, records AGCM_ETIMEOUT (4).
+// Once a wait has given up (err set), later waits return at once, so a fault
+// costs one timeout, not one per level.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int* err) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (err && *(volatile int*)err != 0) return false;
+    if (clock64() - t0 > 2000000000LL) {
+      if (err) atomicExch(err, 4);
+      return false;
+    }
+  }
+  return true;
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// TMA bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+template <class T>
+struct TileCtx {
+  T* buf;           // kStages x 3 fields x kTileRows x kPitch
+  uint64_t* bar;    // kStages mbarriers
+  int H, i0, j0, tx, ty, tid;
+  unsigned tx_bytes;  // bytes one level brings in
+  int* err;
+};
+
+// Issue the copies of level k into stage slot `slot`: per field and staged row
+// one segment of W = 32 + 2H columns starting at i0 - H, split at the seam.
+template <class T>
+__device__ __forceinline__ void tile_issue(const TileCtx<T>& t, const Geom<T>& g, const T* U, const T* Phi,
+                                           const T* V, int k, int slot) {
+  const int I = g.I, J = g.J, W = kTileX + 2 * t.H, c0 = t.i0 - t.H;
+  uint64_t* bar = t.bar + slot;
+  if (t.err && *(volatile int*)t.err != 0) return;  // a wait already gave up: issue nothing more
+  if (t.tid == 0) mbar_arrive_expect_tx(bar, t.tx_bytes);
+  if (t.tid < 36) {
+    const int f = t.tid / 12, r = (t.tid % 12) >> 1, part = t.tid & 1;
+    const int row = t.j0 - 1 + r;
+    const int nrows = f == 2 ? J - 1 : J;
+    if (row >= 0 && row < nrows) {
+      const T* src = (f == 0 ? U : (f == 1 ? Phi : V)) + ((size_t)k * nrows + row) * I;
+      T* dst = t.buf + ((size_t)(slot * 3 + f) * kTileRows + r) * kPitch;
+      int a = 0, len = 0, off = 0;
+      if (part == 0) {
+        a = c0 > 0 ? c0 : 0;
+        const int e = c0 + W < I ? c0 + W : I;
+        len = e - a;
+        off = a - c0;
+      } else if (c0 < 0) {
+        a = I + c0;
+        len = -c0;
+        off = 0;
+      } else if (c0 + W > I) {
+        a = 0;
+        len = c0 + W - I;
+        off = I - c0;
+      }
+      if (len > 0) {
+        fence_proxy_async();
+        bulk_g2s(dst + off, src + a, (unsigned)(len * sizeof(T)), bar);
+      }
+    }
+  }
+}
+
 // The work of one thread: the column (j, i) through all levels of one stage.
 // MODE 0: out = T(xs) (validation); MODE 1: base = xs (first stage);
 // MODE 2: base given (later stages; may alias out).
-template <class T, int MODE>
+// TILE: the level loads come from the shared-memory tile (all threads of the
+// block must call it, inactive ones with clamped indices and active = false);
+// otherwise from global memory.
+// Ubar_b/Vbar_b: vertical means of the base state (FP32 path, MODE > 0): the
+// output's means are base + sum_k dsigma_k (out_k - base_k), the increments
+// being exact differences of stored floats, so no FP64 work runs per level.
+template <class T, int MODE, bool TILE>
 __device__ __forceinline__ void fused_column(
     const Geom<T>& g, const int i, const int j, const T* __restrict__ U, const T* __restrict__ V,
     const T* __restrict__ Phi, const T* __restrict__ pi, const double* __restrict__ Ubar,
     const double* __restrict__ Vbar, const T* Ub, const T* Vb, const T* Phib, const T* pib, T* Uo, T* Vo, T* Phio,
-    T* pio, double* __restrict__ Ubar_o, double* __restrict__ Vbar_o, const T cdt) {
+    T* pio, double* Ubar_o, double* Vbar_o, const double* Ubar_b, const double* Vbar_b, const T cdt,
+    const TileCtx<T>* tc = nullptr, const bool active = true) {
   const int I = g.I, J = g.J, K = g.K;
   const bool hasS = j < J - 1;   // V row j exists, scalar row j+1 exists
   const bool hasN = j > 0;       // V row j-1 exists
@@ -74,6 +184,31 @@ __device__ __forceinline__ void fused_column(
   const int vie = wrapi(i + Mv, I), viw = wrapi(i - Mv, I);
   const int vfE = wrapi(i + (Mv - 1) / 2, I), vfW = wrapi(i - (Mv + 1) / 2, I);
   const int gE = wrapi(i + (M1 - 1) / 2, I), gW = wrapi(i - (M1 + 1) / 2, I);
+
+  // ---- indices of the level loads: shared-memory tile or global rows
+  int lr0 = rj, lrN = rjm, lrS = rjp;
+  int li = i, lie = ie, liw = iw, lfE = fE, lfE1 = fE1, lfW = fW, lfW1 = fW1, lip = ip, lim = im;
+  int lvie = vie, lviw = viw, lvfE = vfE, lvfW = vfW, lgE = gE, lgW = gW;
+  if (TILE) {
+    lr0 = (1 + tc->ty) * kPitch;
+    lrN = tc->ty * kPitch;
+    lrS = (2 + tc->ty) * kPitch;
+    li = tc->tx + tc->H;
+    lie = li + M;
+    liw = li - M;
+    lfE = li + (M - 1) / 2;
+    lfE1 = li + (M + 1) / 2;
+    lfW = li - (M + 1) / 2;
+    lfW1 = li - (M - 1) / 2;
+    lip = li + 1;
+    lim = li - 1;
+    lvie = li + Mv;
+    lviw = li - Mv;
+    lvfE = li + (Mv - 1) / 2;
+    lvfW = li - (Mv + 1) / 2;
+    lgE = li + (M1 - 1) / 2;
+    lgW = li - (M1 + 1) / 2;
+  }
 
   // ---- column state a2 from pi (level independent)
   auto mass = [&](int r, int c) { return g.pit[r + c] + pi[r + c]; };
@@ -135,11 +270,13 @@ __device__ __forceinline__ void fused_column(
     Cs = ((double)PugE * Ubar[rjp + gE] - (double)PugW * Ubar[rjp + gW]) * (double)rdxs +
          ((hasSS ? (double)svjp * (double)Pvs * Vbar[rjp + i] : 0.0) - (double)svj * (double)Pvc * Vbar[rj + i]) *
              (double)rdys;
-  if (MODE == 0)
-    pio[rj + i] = (T)(-Cc);
-  else {
-    const double pb = (MODE == 1) ? (double)pi[rj + i] : (double)pib[rj + i];
-    pio[rj + i] = (T)(pb - (double)cdt * Cc);
+  if (active) {
+    if (MODE == 0)
+      pio[rj + i] = (T)(-Cc);
+    else {
+      const double pb = (MODE == 1) ? (double)pi[rj + i] : (double)pib[rj + i];
+      pio[rj + i] = (T)(pb - (double)cdt * Cc);
+    }
   }
   const T Cf = (T)Cc, Cpf = (T)Cp, Csf = (T)Cs;
 
@@ -149,36 +286,92 @@ __device__ __forceinline__ void fused_column(
   T Wb = 0, Wbp = 0, Wbs = 0;     // W at the bottom face of the current level
   T GsB = 0, GuB = 0, GvB = 0;    // G = F/P one level below
   T PPh = 0, PU = 0, PV = 0;      // partial tendencies of the level below
-  double ubar = 0.0, vbar = 0.0;  // sum dsigma * out (next stage's C)
+  // vertical means of the output (next stage's C): FP64 sums in the FP64
+  // path; base + FP32 sum of increments in the FP32 path
+  constexpr bool kInc = sizeof(T) == 4 && MODE != 0;
+  double ubar = 0.0, vbar = 0.0;
+  T dubar = T(0), dvbar = T(0);
 
-  for (int k = K - 1; k >= -1; --k) {
+  if (TILE) {  // prime the ring with the two lowest levels
+    tile_issue(*tc, g, U, Phi, V, K - 1, 0);
+    if (K >= 2) tile_issue(*tc, g, U, Phi, V, K - 2, 1);
+  }
+  // software pipeline: the geometry of a level is loaded one iteration before
+  // its level is computed, and the base state of a level one iteration before
+  // that level is completed and written
+  T q_ds = g.ds[K - 1], q_H = g.Hkk[K - 1], q_hk = g.hk[K - 1], q_hr = g.hk_rds[K - 1], q_r2 = g.r2ds[K - 1];
+  T q_om = T(1.0 - g.shd[K - 1]);
+  double q_dsd = g.dsd[K - 1];
+  T p_r2 = 0, p_ds = 0;   // level below: 1/(2 dsigma), dsigma
+  double p_dsd = 0.0;
+  T pbU = 0, pbV = 0, pbPh = 0;  // level below: base values
+  const size_t o_own = (size_t)rj + i;
+  int it = 0;
+  for (int k = K - 1; k >= -1; --k, ++it) {
     T Gsc = 0, Guc = 0, Gvc = 0, Wt = 0, Wtp = 0, Wts = 0;
     T nPPh = 0, nPU = 0, nPV = 0;
+    T c_r2 = 0, c_ds = 0, nbU = 0, nbV = 0, nbPh = 0;
+    double c_dsd = 0.0;
     if (k >= 0) {
-      const T* Uk = U + (size_t)k * plane;
-      const T* Phk = Phi + (size_t)k * plane;
-      const T* Vk = V + (size_t)k * vplane;
-      const T dsk = g.ds[k], Hkk = g.Hkk[k], hk = g.hk[k], hkr = g.hk_rds[k], r2dsk = g.r2ds[k];
-      const T onems = T(1.0 - g.shd[k]);
+      if (MODE == 2) {  // base of this level, used when it is completed next iteration
+        nbU = Ub[(size_t)k * plane + o_own];
+        nbPh = Phib[(size_t)k * plane + o_own];
+        if (hasS) nbV = Vb[(size_t)k * vplane + o_own];
+      }
+      const T* Uk;
+      const T* Phk;
+      const T* Vk;
+      if (TILE) {
+        // the slot of level k+1 was released at the end of the last iteration
+        if (k >= 2) tile_issue(*tc, g, U, Phi, V, k - 2, (it + 2) % kStages);
+        const int slot = it % kStages;
+        mbar_wait(tc->bar + slot, (unsigned)((it / kStages) & 1), tc->err);
+        const T* sb = tc->buf + (size_t)slot * 3 * kTileRows * kPitch;
+        Uk = sb;
+        Phk = sb + kTileRows * kPitch;
+        Vk = sb + 2 * kTileRows * kPitch;
+      } else {
+        Uk = U + (size_t)k * plane;
+        Phk = Phi + (size_t)k * plane;
+        Vk = V + (size_t)k * vplane;
+      }
+      const T dsk = q_ds, Hkk = q_H, hk = q_hk, hkr = q_hr, r2dsk = q_r2, onems = q_om;
+      c_r2 = q_r2;
+      c_ds = q_ds;
+      c_dsd = q_dsd;
+      if (k >= 1) {
+        q_ds = g.ds[k - 1];
+        q_H = g.Hkk[k - 1];
+        q_hk = g.hk[k - 1];
+        q_hr = g.hk_rds[k - 1];
+        q_r2 = g.r2ds[k - 1];
+        q_om = T(1.0 - g.shd[k - 1]);
+        q_dsd = g.dsd[k - 1];
+      }
       // loads
-      const T Phc = Phk[rj + i], Phe = Phk[rj + ie], Phw = Phk[rj + iw];
-      const T PhE1 = Phk[rj + fE1], PhW1 = Phk[rj + fW1];
-      const T Phs = hasS ? Phk[rjp + i] : T(0), Phn = hasN ? Phk[rjm + i] : T(0);
-      const T Uc = Uk[rj + i], Ue = Uk[rj + ie], Uw = Uk[rj + iw], Um = Uk[rj + im];
-      const T UfE = Uk[rj + fE], UfE1 = Uk[rj + fE1], UfW = Uk[rj + fW], UfW1 = Uk[rj + fW1];
-      const T Us = hasS ? Uk[rjp + i] : T(0), Un = hasN ? Uk[rjm + i] : T(0);
+      const T Phc = Phk[lr0 + li], Phe = Phk[lr0 + lie], Phw = Phk[lr0 + liw];
+      const T PhE1 = Phk[lr0 + lfE1], PhW1 = Phk[lr0 + lfW1];
+      const T Phs = hasS ? Phk[lrS + li] : T(0), Phn = hasN ? Phk[lrN + li] : T(0);
+      const T Uc = Uk[lr0 + li], Ue = Uk[lr0 + lie], Uw = Uk[lr0 + liw], Um = Uk[lr0 + lim];
+      const T UfE = Uk[lr0 + lfE], UfE1 = Uk[lr0 + lfE1], UfW = Uk[lr0 + lfW], UfW1 = Uk[lr0 + lfW1];
+      const T Us = hasS ? Uk[lrS + li] : T(0), Un = hasN ? Uk[lrN + li] : T(0);
       T Vc = 0, Vp = 0, Ve = 0, Vw = 0, Vn = 0, Vnp = 0, Vs = 0;
       if (hasS) {
-        Vc = Vk[rj + i];
-        Vp = Vk[rj + ip];
-        Ve = Vk[rj + vie];
-        Vw = Vk[rj + viw];
+        Vc = Vk[lr0 + li];
+        Vp = Vk[lr0 + lip];
+        Ve = Vk[lr0 + lvie];
+        Vw = Vk[lr0 + lviw];
       }
       if (hasN) {
-        Vn = Vk[rjm + i];
-        Vnp = Vk[rjm + ip];
+        Vn = Vk[lrN + li];
+        Vnp = Vk[lrN + lip];
       }
-      if (hasSS) Vs = Vk[rjp + i];
+      if (hasSS) Vs = Vk[lrS + li];
+      if (MODE == 1) {
+        nbU = Uc;
+        nbPh = Phc;
+        nbV = Vc;
+      }
       // mass fluxes
       const T FlE = PufE * UfE, FlE1 = PufE1 * UfE1, FlW = PufW * UfW, FlW1 = PufW1 * UfW1;
       const T Ftc = Pvc * Vc, Ftp = Pvp * Vp, Ftn = Pvn * Vn, Ftnp = Pvnp * Vnp, Fts = Pvs * Vs;
@@ -186,7 +379,7 @@ __device__ __forceinline__ void fused_column(
       const T D = (FlE - FlW) * rdx + (svj * Ftc - svjm * Ftn) * rdy;
       const T Dp = (FlE1 - FlW1) * rdx + (svj * Ftp - svjm * Ftnp) * rdy;
       T Ds = 0;
-      if (hasS) Ds = (PugE * Uk[rjp + gE] - PugW * Uk[rjp + gW]) * rdxs + (svjp * Fts - svj * Ftc) * rdys;
+      if (hasS) Ds = (PugE * Uk[lrS + lgE] - PugW * Uk[lrS + lgW]) * rdxs + (svjp * Fts - svj * Ftc) * rdys;
       // a4: suffix sums -> W at the top face of level k
       SD += dsk * D;
       SDp += dsk * Dp;
@@ -224,8 +417,8 @@ __device__ __forceinline__ void fused_column(
       // ---- V cell
       if (hasS) {
         Gvc = Vc * rPvc;
-        const T UvE = Uk[rj + vfE], UvW = Uk[rj + vfW], UsvE = Uk[rjp + vfE], UsvW = Uk[rjp + vfW];
-        const T Usm = Uk[rjp + im];
+        const T UvE = Uk[lr0 + lvfE], UvW = Uk[lr0 + lvfW], UsvE = Uk[lrS + lvfE], UsvW = Uk[lrS + lvfW];
+        const T Usm = Uk[lrS + lim];
         const T ZE = zfv * T(0.5) * (PuvE * UvE + PusvE * UsvE);
         const T ZW = zfv * T(0.5) * (PuvW * UvW + PusvW * UsvW);
         T hor = ZE * Ve * rPve - ZW * Vw * rPvw;
@@ -244,33 +437,31 @@ __device__ __forceinline__ void fused_column(
     // ---- complete level k+1 with its top-face vertical term (needs G_k) and write it
     if (k + 1 <= K - 1) {
       const int kk = k + 1;
-      const T r2dsk1 = g.r2ds[kk];
+      const T r2dsk1 = p_r2;
       const T TPh = PPh + Wb * Gsc * r2dsk1 * rPc;
       const T TU = PU + T(0.5) * (Wb + Wbp) * Guc * r2dsk1 * rPuc;
       const size_t o = (size_t)kk * plane + rj + i;
-      T bPh, bU;
-      if (MODE == 0) {
-        bPh = T(0);
-        bU = T(0);
-      } else if (MODE == 1) {
-        bPh = Phi[o];
-        bU = U[o];
-      } else {
-        bPh = Phib[o];
-        bU = Ub[o];
-      }
+      const T bPh = MODE == 0 ? T(0) : pbPh, bU = MODE == 0 ? T(0) : pbU;
       const T oPh = bPh + cdt * TPh, oU = bU + cdt * TU;
-      Phio[o] = oPh;
-      Uo[o] = oU;
-      const double dsk1 = g.dsd[kk];
-      ubar += dsk1 * (double)oU;
+      if (active) {
+        Phio[o] = oPh;
+        Uo[o] = oU;
+      }
+      if (kInc) {
+        dubar += p_ds * (oU - bU);
+      } else {
+        ubar += p_dsd * (double)oU;
+      }
       if (hasS) {
         const T TV = PV + T(0.5) * (Wb + Wbs) * Gvc * r2dsk1 * rPvc;
         const size_t ov = (size_t)kk * vplane + rj + i;
-        const T bV = (MODE == 0) ? T(0) : (MODE == 1 ? V[ov] : Vb[ov]);
+        const T bV = MODE == 0 ? T(0) : pbV;
         const T oV = bV + cdt * TV;
-        Vo[ov] = oV;
-        vbar += dsk1 * (double)oV;
+        if (active) Vo[ov] = oV;
+        if (kInc)
+          dvbar += p_ds * (oV - bV);
+        else
+          vbar += p_dsd * (double)oV;
       }
     }
     PPh = nPPh;
@@ -282,24 +473,87 @@ __device__ __forceinline__ void fused_column(
     Wb = Wt;
     Wbp = Wtp;
     Wbs = Wts;
+    p_r2 = c_r2;
+    p_ds = c_ds;
+    p_dsd = c_dsd;
+    pbU = nbU;
+    pbV = nbV;
+    pbPh = nbPh;
+    if (TILE && k >= 0) __syncthreads();  // every thread is done with this level's slot
   }
-  if (Ubar_o) {
+  if (Ubar_o && active) {
+    if (kInc) {
+      ubar = Ubar_b[rj + i] + (double)dubar;
+      if (hasS) vbar = Vbar_b[rj + i] + (double)dvbar;
+    }
     Ubar_o[rj + i] = ubar;
     if (hasS) Vbar_o[rj + i] = vbar;
   }
 }
 
-template <class T, int MODE>
-__global__ void __launch_bounds__(kFusedBX * kFusedBY, sizeof(T) == 4 ? AGCM_FUSED_MINB : AGCM_FUSED_MINB64)
+// BY = 1: one warp per block covering 32 columns of one row, loads from
+// global memory (the row index is warp-uniform, so row tables sit in uniform
+// registers).  BY = kTileY: a 32 x 4 tile whose levels are staged in shared
+// memory by the TMA bulk-copy engine (global loads where the halo is too wide).
+template <class T, int MODE, int BY>
+__global__ void __launch_bounds__(kTileX* BY, BY == 1 ? (sizeof(T) == 4 ? AGCM_FUSED_MINB : AGCM_FUSED_MINB64)
+                                                      : (sizeof(T) == 4 ? AGCM_TILE_MINB : 2))
     k_fused_stage(Geom<T> g, const T* __restrict__ U, const T* __restrict__ V, const T* __restrict__ Phi,
                   const T* __restrict__ pi, const double* __restrict__ Ubar, const double* __restrict__ Vbar,
                   const T* Ub, const T* Vb, const T* Phib, const T* pib, T* Uo, T* Vo, T* Phio, T* pio,
-                  double* __restrict__ Ubar_o, double* __restrict__ Vbar_o, T cdt) {
-  const int i = blockIdx.x * kFusedBX + threadIdx.x;
-  const int j = kFusedBY == 1 ? (int)blockIdx.y : (int)(blockIdx.y * kFusedBY + threadIdx.y);
-  if (i >= g.I || j >= g.J) return;
-  fused_column<T, MODE>(g, i, j, U, V, Phi, pi, Ubar, Vbar, Ub, Vb, Phib, pib, Uo, Vo, Phio, pio, Ubar_o, Vbar_o,
-                        cdt);
+                  double* Ubar_o, double* Vbar_o, const double* Ubar_b, const double* Vbar_b, T cdt,
+                  int tile_enable, int* err) {
+  const int tx = threadIdx.x;
+  if (BY == 1) {
+    const int i = blockIdx.x * kTileX + tx, j = blockIdx.y;
+    if (i < g.I)
+      fused_column<T, MODE, false>(g, i, j, U, V, Phi, pi, Ubar, Vbar, Ub, Vb, Phib, pib, Uo, Vo, Phio, pio, Ubar_o,
+                                   Vbar_o, Ubar_b, Vbar_b, cdt);
+    return;
+  }
+  const int ty = threadIdx.y;
+  const int i0 = blockIdx.x * kTileX, j0 = blockIdx.y * BY;
+  const int i = i0 + tx, j = j0 + ty;
+  const bool active = i < g.I && j < g.J;
+  // halo: the largest stride of the scalar and V rows this tile touches, + 1, to a multiple of 4
+  int Mmax = 1;
+  for (int r = j0 - 1; r <= j0 + BY; ++r) {
+    if (r >= 0 && r < g.J) Mmax = max(Mmax, g.Mu[r]);
+    if (r >= 0 && r < g.J - 1) Mmax = max(Mmax, g.Mv[r]);
+  }
+  const int H = (Mmax + 4) & ~3;
+  const bool tile = tile_enable && H <= kHaloMax && (g.I % 4) == 0 && kTileX + 2 * H <= g.I;
+  if (!tile) {
+    if (active)
+      fused_column<T, MODE, false>(g, i, j, U, V, Phi, pi, Ubar, Vbar, Ub, Vb, Phib, pib, Uo, Vo, Phio, pio, Ubar_o,
+                                   Vbar_o, Ubar_b, Vbar_b, cdt);
+    return;
+  }
+  extern __shared__ __align__(128) unsigned char smem[];
+  TileCtx<T> t;
+  t.bar = reinterpret_cast<uint64_t*>(smem);
+  t.buf = reinterpret_cast<T*>(smem + 64);
+  t.H = H;
+  t.i0 = i0;
+  t.j0 = j0;
+  t.tx = tx;
+  t.ty = ty;
+  t.tid = ty * kTileX + tx;
+  t.err = err;
+  int rows_s = 0, rows_v = 0;
+  for (int r = 0; r < kTileRows; ++r) {
+    const int row = j0 - 1 + r;
+    rows_s += (row >= 0 && row < g.J) ? 1 : 0;
+    rows_v += (row >= 0 && row < g.J - 1) ? 1 : 0;
+  }
+  t.tx_bytes = (unsigned)((2 * rows_s + rows_v) * (kTileX + 2 * H) * sizeof(T));
+  if (t.tid == 0) {
+    for (int q = 0; q < kStages; ++q) mbar_init(t.bar + q, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  fused_column<T, MODE, true>(g, min(i, g.I - 1), min(j, g.J - 1), U, V, Phi, pi, Ubar, Vbar, Ub, Vb, Phib, pib,
+                              Uo, Vo, Phio, pio, Ubar_o, Vbar_o, Ubar_b, Vbar_b, cdt, &t, active);
 }
 
 // Vertical means Ubar = sum_k dsigma_k U_k, Vbar likewise (FP64), of a state.

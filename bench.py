@@ -331,7 +331,7 @@ def measure_forms(agcm, inputs, torch, steps=5):
     return out
 
 
-def measure_ensemble(agcm, inputs, torch, steps=10):
+def measure_ensemble(agcm, inputs, torch, steps=10, per_member=True):
     """Config 4: 32 @ 256x128x30 + 24 @ 360x180x30 + 8 @ 720x360x30, FP32,
     one persistent launch per call, autotuned and replayed from a CUDA graph;
     against 64 per-member launches of the plain FP64 step."""
@@ -366,6 +366,8 @@ def measure_ensemble(agcm, inputs, torch, steps=10):
     ens.close()
     for s in states:
         s.close()
+    if not per_member:
+        return res
     # per-member launches of the plain FP64 step
     s64 = []
     for (g, st) in grids:

@@ -180,15 +180,15 @@ const char* agcm_kernel_name(int id);
  * them).  agcm_ensemble_step advances every member nsteps steps of the
  * three-stage scheme (dt[m] seconds for member m) in one kernel launch whose
  * blocks pull (member, row segment) work items from a device queue; member m
- * does the same arithmetic as agcm_step on it (results agree to the last bit
- * in FP32 and to a few ulp in FP64, where multiply-add contraction may differ).  Stages are separated
+ * does the same arithmetic as agcm_step on it (results agree to about one
+ * rounding: the two kernels may contract multiply-adds differently).  Stages are separated
  * by grid barriers whose waits are bounded by the timeout (default 1 s): if a
  * wait runs out the kernel stops and agcm_ensemble_status reports
  * AGCM_ETIMEOUT (this happens only if not all blocks can be resident at once,
  * e.g. when other work occupies the GPU).  The launch can be captured in a
  * CUDA graph once a first call has uploaded the dt values (nsteps = 0 only
  * prepares: it uploads dt and the members' vertical means without stepping).
- * agcm_ensemble_configure sets the launch shape (warps per block 1..4, blocks
+ * agcm_ensemble_configure sets the launch shape (warps per block: 1; blocks
  * per SM, 0 = as many as fit); an autotuner picks it (ensemble.py).
  * agcm_ensemble_set_timeout: barrier timeout in seconds; test_missing_blocks
  * > 0 makes every barrier wait for blocks that do not exist, to exercise the

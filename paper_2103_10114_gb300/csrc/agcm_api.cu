@@ -1081,7 +1081,7 @@ struct agcm_ensemble {
   agcm::EnsSync* d_sync = nullptr;
   int queue_cap = 0;             // steps per launch
   int nitems = 0;
-  int warps_per_block = 4;
+  int warps_per_block = 1;
   int blocks_per_sm = 0;         // 0: as many as fit
   double timeout_s = 1.0;
   int test_missing = 0;
@@ -1206,8 +1206,8 @@ int agcm_ensemble_destroy(agcm_ensemble_t* e) {
 }
 
 int agcm_ensemble_configure(agcm_ensemble_t* e, int warps_per_block, int blocks_per_sm) {
-  if (!e || warps_per_block < 1 || warps_per_block > 4 || blocks_per_sm < 0)
-    return fail(AGCM_EINVAL, "warps_per_block must be 1..4 and blocks_per_sm >= 0");
+  if (!e || warps_per_block != 1 || blocks_per_sm < 0)
+    return fail(AGCM_EINVAL, "warps_per_block must be 1 and blocks_per_sm >= 0");
   e->warps_per_block = warps_per_block;
   e->blocks_per_sm = blocks_per_sm;
   return AGCM_OK;

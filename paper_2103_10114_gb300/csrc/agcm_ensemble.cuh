@@ -4,8 +4,9 @@
 // 32 columns of one member; each warp pulls items from a per-(step, stage)
 // device counter and runs the same column body as the single-state stage
 // kernel (fused_column), so a member advanced in an ensemble does the same
-// arithmetic as alone (bit-identical in FP32 on GB300; in FP64 the compiler
-// may contract multiply-adds differently in the two kernels, a few ulp).  Stages are separated by a grid-wide barrier whose
+// arithmetic as alone; the two kernels are compiled separately, so the
+// compiler may contract multiply-adds differently (results agree to about
+// one FP32 / FP64 rounding, not to the bit).  Stages are separated by a grid-wide barrier whose
 // wait is bounded in time: if it runs out, the kernel records AGCM_ETIMEOUT in
 // the status word and every block returns; nothing spins forever and nothing
 // traps.  The launch is sized so that every block is resident at once.
@@ -77,11 +78,23 @@ __device__ __forceinline__ int ens_member_of(const EnsMember<T>* mem, int nmem, 
   return lo;
 }
 
+// One warp per block (the stage kernel's shape); the register cap of 12
+// resident blocks per SM (168 registers) measured fastest for the 64-member
+// mix on GB300 (20 -> 18.1 ms/step, 16 -> 14.4, 12 -> 12.6); the autotuner
+// varies the number of resident blocks per SM.
+#ifndef AGCM_ENS_MINB
+#define AGCM_ENS_MINB 12
+#endif
 template <class T>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2)
+__global__ void __launch_bounds__(32, sizeof(T) == 4 ? AGCM_ENS_MINB : 8)
     k_ensemble(const EnsMember<T>* __restrict__ mem, int nmem, int nitems, int nsteps, EnsSync* sy,
                unsigned expected_blocks, long long limit) {
   const int lane = threadIdx.x & 31;
+  // the current member's descriptor, copied to shared memory per work item so
+  // that its pointers are re-read cheaply instead of held in registers
+  __shared__ __align__(16) unsigned long long sdesc[(sizeof(EnsMember<T>) + 7) / 8];
+  const EnsMember<T>& e = *reinterpret_cast<const EnsMember<T>*>(sdesc);
+  int cur = -1;
   for (int step = 0; step < nsteps; ++step) {
     for (int stage = 0; stage < 3; ++stage) {
       unsigned int* q = &sy->queue[step * 3 + stage];
@@ -91,24 +104,26 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2)
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= nitems) break;
         const int m = ens_member_of(mem, nmem, item);
-        const EnsMember<T>& e = mem[m];
+        if (m != cur) {
+          __syncwarp();
+          const unsigned long long* src = reinterpret_cast<const unsigned long long*>(mem + m);
+          for (int w = lane; w < (int)((sizeof(EnsMember<T>) + 7) / 8); w += 32) sdesc[w] = src[w];
+          __syncwarp();
+          cur = m;
+        }
         const int local = item - e.item_begin;
         const int j = local / e.nbx;
         const int i = (local - j * e.nbx) * 32 + lane;
         if (i < e.g.I) {
           const Geom<T>& g = e.g;
-          if (stage == 0) {
-            fused_column<T, 1, false>(g, i, j, e.x[0][0], e.x[0][1], e.x[0][2], e.x[0][3], e.ubar[0], e.vbar[0],
-                                      nullptr, nullptr, nullptr, nullptr, e.x[1][0], e.x[1][1], e.x[1][2],
-                                      e.x[1][3], e.ubar[1], e.vbar[1], e.ubar[0], e.vbar[0], T(0.5) * e.dt);
-          } else {
-            // stage 2: x1 -> x2; stage 3: x2 -> x_n in place; base x_n in both
-            const int a = stage, b = stage == 1 ? 2 : 0;
-            const T c = stage == 1 ? T(0.5) * e.dt : e.dt;
-            fused_column<T, 2, false>(g, i, j, e.x[a][0], e.x[a][1], e.x[a][2], e.x[a][3], e.ubar[a], e.vbar[a],
-                                      e.x[0][0], e.x[0][1], e.x[0][2], e.x[0][3], e.x[b][0], e.x[b][1], e.x[b][2],
-                                      e.x[b][3], e.ubar[b], e.vbar[b], e.ubar[0], e.vbar[0], c);
-          }
+          // stage 1: x_n -> x1 (dt/2); stage 2: x1 -> x2 (dt/2); stage 3: x2 -> x_n
+          // in place (dt); the base is x_n in all three (stage 1 reads it
+          // as base instead of reusing its own values: the same arithmetic)
+          const int a = stage, b = stage == 0 ? 1 : (stage == 1 ? 2 : 0);
+          const T c = stage == 2 ? e.dt : T(0.5) * e.dt;
+          fused_column<T, 2, false>(g, i, j, e.x[a][0], e.x[a][1], e.x[a][2], e.x[a][3], e.ubar[a], e.vbar[a],
+                                    e.x[0][0], e.x[0][1], e.x[0][2], e.x[0][3], e.x[b][0], e.x[b][1], e.x[b][2],
+                                    e.x[b][3], e.ubar[b], e.vbar[b], e.ubar[0], e.vbar[0], c);
         }
       }
       __threadfence();

@@ -1,8 +1,9 @@
 """Ensembles of members of uneven resolution: one persistent launch per call,
 an autotuner for its launch shape, and CUDA-graph replay.
 
-The launch shape (warps per block, blocks per SM) decides how the work items
-(32-column row segments of every member) are spread over the SMs; the best
+The launch shape (one-warp blocks, how many resident per SM) decides how the
+work items (32-column row segments of every member) are spread over the SMs
+and how many warps hide each other's memory latency; the best
 shape depends on the member mix and the GPU, so `autotune` times each
 candidate on the ensemble itself and keeps the fastest (cached per member mix
 and device name for the life of the process).
@@ -23,7 +24,7 @@ class Ensemble:
         h = ctypes.c_void_p()
         agcm.check(agcm.lib().agcm_ensemble_create(arr, len(self.states), ctypes.byref(h)))
         self._h = h
-        self.shape = (4, 0)
+        self.shape = (1, 0)
 
     @property
     def handle(self):
@@ -71,7 +72,7 @@ class Ensemble:
             self.configure(*_TUNE_CACHE[key])
             return _TUNE_CACHE[key], {}
         if candidates is None:
-            candidates = [(w, b) for w in (1, 2, 4) for b in (0, 2, 4, 8) if not (w == 1 and b in (2, 4))]
+            candidates = [(1, b) for b in (0, 8, 12, 16, 20, 24)]
         saved = [s.store() for s in self.states]
         times = {}
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

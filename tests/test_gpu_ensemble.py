@@ -46,12 +46,12 @@ def test_member_equals_single_run(prec):
         alone.load(st)
         alone.step(3, dt)
         want = np_state(alone)
+        # the same column body in two kernels: the compiler may fuse
+        # multiply-adds differently, so agreement is to about one rounding
+        tol = 1e-6 if prec == agcm.AGCM_FP32 else 1e-13
         for f in FIELDS:
-            if prec == agcm.AGCM_FP32:  # same kernel body: identical bits
-                assert np.array_equal(got[f], want[f]), (g.nlon, f, np.abs(got[f] - want[f]).max())
-            else:  # FP64: the compiler may fuse multiply-adds differently in the two kernels
-                err = np.abs(got[f] - want[f]).max() / np.abs(want[f]).max()
-                assert err <= 1e-13, (g.nlon, f, err)
+            err = np.abs(got[f] - want[f]).max() / np.abs(want[f]).max()
+            assert err <= tol, (g.nlon, f, err)
     ens.close()
 
 

@@ -117,6 +117,22 @@ def dist_setup():
     return 0, 1, 0
 
 
+def max_over_ranks(value, device):
+    """Largest value over all ranks (timing is the slowest rank's); identity on one rank."""
+    import torch
+
+    if not torch.distributed.is_available() or not torch.distributed.is_initialized():
+        return float(value)
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(points_per_rank, steps, ms_max, world):
+    """Replicas: every rank advances its own state; the job's rate is the sum."""
+    return world * points_per_rank * steps / (ms_max / 1e3)
+
+
 def cpu_oracle_rate(nlon, nlat, nlev, steps=1, st=None):
     """Time the FP64 oracle on one grid; returns (gp-steps/s, seconds)."""
     import oracle
@@ -165,9 +181,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--only", choices=["adjoint", "ensemble", "fp64"],
+                    help="measure one form alone and print its JSON (for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.only:
+        return run_only(args.only)
 
     import numpy as np
     import torch
@@ -209,11 +229,8 @@ def main():
     prof = s.profile_read()
     s.profile(False)
     clocks = clk.summary()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * pts * args.steps / (ms / 1e3)
+    ms = max_over_ranks(ms, "cuda")
+    value = whole_job_rate(pts, args.steps, ms, world)
     d = s.diagnostics()
 
     # end to end through the C ABI with pinned host buffers
@@ -232,11 +249,8 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e = world * pts * e2e_steps / (e2e_ms / 1e3)
+    e2e_ms = max_over_ranks(e2e_ms, "cuda")
+    e2e = whole_job_rate(pts, e2e_steps, e2e_ms, world)
 
     peak, peak_kind = peaks()
     # dominant kernel and its algorithmic bytes (one stage: 6/9/9 words per point -> 8 on average)
@@ -278,6 +292,29 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_only(form):
+    import torch
+
+    from paper_2103_10114_gb300 import agcm, inputs
+
+    agcm.build()
+    agcm.lib()
+    if form == "adjoint":
+        out = measure_adjoint(agcm, inputs, torch, steps=3)
+    elif form == "ensemble":
+        out = measure_ensemble(agcm, inputs, torch, steps=3, per_member=False)
+    else:
+        I, J, K = WORKLOAD
+        st = inputs.baroclinic_jet(I, J, K, seed=6, noise=1e-2, terrain_seed=2)
+        g = agcm.Grid(I, J, K, phis=st["phis"])
+        s = agcm.State(g, agcm.AGCM_FP64)
+        s.load(st)
+        s.step(1, g.dt(100.0))
+        ms = _time(torch, lambda: s.step(2, g.dt(100.0)), 1) / 2
+        out = {"value": I * J * K / (ms / 1e3), "unit": "gp-steps/s", "ms_per_step": ms}
+    print(json.dumps({"form": form, **out}), flush=True)
 
 
 def _time(torch, fn, reps):

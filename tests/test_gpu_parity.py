@@ -178,3 +178,45 @@ def test_full_size_one_step_fp32():
     ref = oracle.Oracle(I, J, K, phis=st["phis"]).step(st, dt, 1)
     for f in FIELDS:
         assert rel_err(out[f], ref[f]) <= 1e-5, (f, rel_err(out[f], ref[f]))
+
+
+def test_allocation_failure_is_reported_and_leaks_nothing():
+    """An allocator that refuses after a few allocations: agcm_state_create
+    returns AGCM_ENOMEM and frees what it had; the default allocator then works."""
+    import ctypes
+
+    L = agcm.lib()
+    calls = {"n": 0, "live": set()}
+
+    def alloc(n, ctx):
+        calls["n"] += 1
+        if calls["n"] > 5:
+            return None
+        import torch
+
+        p = torch.cuda.caching_allocator_alloc(int(n))
+        calls["live"].add(p)
+        return p
+
+    def free(p, ctx):
+        import torch
+
+        calls["live"].discard(p)
+        torch.cuda.caching_allocator_delete(p)
+
+    A = agcm._ALLOC_T(alloc)
+    F = agcm._FREE_T(free)
+    agcm.check(L.agcm_set_allocator(ctypes.cast(A, ctypes.c_void_p), ctypes.cast(F, ctypes.c_void_p), None))
+    try:
+        g = agcm.Grid(24, 12, 3)
+        h = ctypes.c_void_p()
+        rc = L.agcm_state_create(g.handle, agcm.AGCM_FP64, 1, ctypes.byref(h))
+        assert rc == agcm.AGCM_ENOMEM
+        assert "allocation" in L.agcm_last_error().decode()
+        live_after = len(calls["live"])
+        assert live_after <= 1  # only the grid's tables stay (owned by the grid)
+    finally:
+        agcm._alloc_cbs = None
+        agcm.use_torch_allocator()
+    s = agcm.State(g, agcm.AGCM_FP64)
+    s.close()

@@ -181,7 +181,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
-    ap.add_argument("--only", choices=["adjoint", "ensemble", "fp64"],
+    ap.add_argument("--only", choices=["adjoint", "ensemble", "fp64", "split"],
                     help="measure one form alone and print its JSON (for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -305,6 +305,8 @@ def run_only(form):
         out = measure_adjoint(agcm, inputs, torch, steps=3)
     elif form == "ensemble":
         out = measure_ensemble(agcm, inputs, torch, steps=3, per_member=False)
+    elif form == "split":
+        out = measure_split(agcm, inputs, torch, steps=3)
     else:
         I, J, K = WORKLOAD
         st = inputs.baroclinic_jet(I, J, K, seed=6, noise=1e-2, terrain_seed=2)
@@ -358,6 +360,10 @@ def measure_forms(agcm, inputs, torch, steps=5):
                                     "note": "state fits in L2"}
         s2.close()
     try:
+        out["split_1440x720x30"] = measure_split(agcm, inputs, torch)
+    except Exception as e:
+        out["split_1440x720x30"] = {"error": repr(e)}
+    try:
         out["ensemble_64"] = measure_ensemble(agcm, inputs, torch)
     except Exception as e:  # reported, not hidden
         out["ensemble_64"] = {"error": repr(e)}
@@ -366,6 +372,28 @@ def measure_forms(agcm, inputs, torch, steps=5):
     except Exception as e:
         out["adjoint_720x360x30"] = {"error": repr(e)}
     return out
+
+
+def measure_split(agcm, inputs, torch, steps=5):
+    """Split stepping at 1440x720x30 FP32: msub adaptation steps of dt/msub and
+    one advection step of dt per step (dt from the flow speed alone)."""
+    I, J, K = WORKLOAD
+    st = inputs.baroclinic_jet(I, J, K, seed=6, noise=1e-2, terrain_seed=2)
+    g = agcm.Grid(I, J, K, phis=st["phis"])
+    dt, msub = g.dt_split(100.0)
+    s = agcm.State(g, agcm.AGCM_FP32)
+    s.load(st)
+    s.step_split(1, dt, msub)
+    ms = _time(torch, lambda: s.step_split(steps, dt, msub), 1) / steps
+    pts = I * J * K
+    words = 24 * msub + 24
+    res = {"value": pts / (ms / 1e3), "unit": "gp-steps/s", "ms_per_step": ms, "dt_s": dt, "msub": msub,
+           "bytes_per_point_step": words * 4,
+           "hbm_frac_step": pts / (ms / 1e3) * words * 4 / (peaks()[0] * 1e9),
+           "sypd_equiv": pts / (ms / 1e3) / pts * dt / 365.0,
+           "finite": bool(s.diagnostics()["finite"])}
+    s.close()
+    return res
 
 
 def measure_ensemble(agcm, inputs, torch, steps=10, per_member=True):

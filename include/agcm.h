@@ -130,6 +130,19 @@ int agcm_state_store(const agcm_state_t* state, void* U, void* V, void* Phi, voi
 int agcm_step(agcm_state_t* state, int nsteps, double dt, void* stream);
 
 /*
+ * agcm_step_split — split time stepping (Sec. "Optimizations": per step the
+ * adaptation process is called 3*M times and the advection process 3 times;
+ * reading the labels as A = adaptation, L = advection): each of the nsteps
+ * steps runs msub three-stage steps of the adaptation terms (pressure
+ * gradient, Coriolis pair, Omega~ conversion, dpi/dt) with dt/msub, then one
+ * three-stage step of the advection terms with dt.  1 <= msub <= 64.
+ * agcm_grid_dt_split: dt from the advective bound alone (flow speed umax) and
+ * msub = ceil(dt / gravity-wave dt).  Host only.
+ */
+int agcm_step_split(agcm_state_t* state, int nsteps, double dt, int msub, void* stream);
+int agcm_grid_dt_split(const agcm_grid_t* grid, double umax, double* dt, int* msub);
+
+/*
  * agcm_tendency — T(x) of the current state into caller-owned device
  * buffers (same layout and element type as the state).  For validation.
  */

@@ -76,6 +76,8 @@ SIGNATURES = {
     "agcm_state_store": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _vp]),
     "agcm_step": (_i, [_vp, _i, _d, _vp]),
     "agcm_tendency": (_i, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "agcm_step_split": (_i, [_vp, _i, _d, _i, _vp]),
+    "agcm_grid_dt_split": (_i, [_vp, _d, _pd, ctypes.POINTER(ctypes.c_int)]),
     "agcm_step_adjoint": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _d, _vp]),
     "agcm_diagnostics": (_i, [_vp, _vp, _vp]),
     "agcm_profile_enable": (_i, [_vp, _i]),
@@ -181,6 +183,12 @@ class Grid:
         check(lib().agcm_grid_dt(self._h, float(umax), ctypes.byref(out)))
         return out.value
 
+    def dt_split(self, umax=100.0):
+        """(advective dt, adaptation sub-steps per step) for agcm_step_split."""
+        dt, m = ctypes.c_double(), ctypes.c_int()
+        check(lib().agcm_grid_dt_split(self._h, float(umax), ctypes.byref(dt), ctypes.byref(m)))
+        return dt.value, m.value
+
     def shapes(self):
         K, J, I = self.nlev, self.nlat, self.nlon
         return {"U": (K, J, I), "V": (K, J - 1, I), "Phi": (K, J, I), "pi": (J, I)}
@@ -257,6 +265,9 @@ class State:
 
     def step(self, nsteps, dt, stream=None):
         check(lib().agcm_step(self._h, int(nsteps), float(dt), _stream_ptr(stream)))
+
+    def step_split(self, nsteps, dt, msub, stream=None):
+        check(lib().agcm_step_split(self._h, int(nsteps), float(dt), int(msub), _stream_ptr(stream)))
 
     def tendency(self, stream=None):
         out = self.empty()

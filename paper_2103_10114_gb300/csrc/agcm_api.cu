@@ -383,20 +383,20 @@ int ensure_bar(agcm_state* s, cudaStream_t st) {
 #ifndef AGCM_STAGE_TILE
 #define AGCM_STAGE_TILE 0
 #endif
-template <class T, int MODE>
+template <class T, int MODE, int TERMS = 3>
 int launch_fused(const agcm::Geom<T>& G, const void* const xs[4], const double* ub, const double* vb,
                  const void* const xb[4], void* const out[4], double* ubo, double* vbo, const double* ubb,
                  const double* vbb, double cdt, int* err, cudaStream_t st) {
-  if (!AGCM_STAGE_TILE) {
+  if constexpr (!AGCM_STAGE_TILE || TERMS != 3) {
     const dim3 block(agcm::kTileX, 1);
     const dim3 grid((unsigned)((G.I + agcm::kTileX - 1) / agcm::kTileX), (unsigned)G.J);
-    agcm::k_fused_stage<T, MODE, 1><<<grid, block, 0, st>>>(
+    agcm::k_fused_stage<T, MODE, 1, TERMS><<<grid, block, 0, st>>>(
         G, (const T*)xs[0], (const T*)xs[1], (const T*)xs[2], (const T*)xs[3], ub, vb, (const T*)xb[0],
         (const T*)xb[1], (const T*)xb[2], (const T*)xb[3], (T*)out[0], (T*)out[1], (T*)out[2], (T*)out[3], ubo, vbo,
         ubb, vbb, (T)cdt, 0, err);
     CUDA_TRY(cudaGetLastError());
     return AGCM_OK;
-  }
+  } else {
   static bool attr_set = false;  // per process; the attribute is per function
   const size_t smem = agcm::tile_smem_bytes<T>();
   if (!attr_set) {
@@ -417,13 +417,14 @@ int launch_fused(const agcm::Geom<T>& G, const void* const xs[4], const double* 
       ubb, vbb, (T)cdt, tile, err);
   CUDA_TRY(cudaGetLastError());
   return AGCM_OK;
+  }
 }
 
-template <class T, int MODE>
+template <class T, int MODE, int TERMS = 3>
 int fused_stage(agcm_state* s, int in, void* const out[4], int outb, double cdt, cudaStream_t st) {
   const agcm::Geom<T>& G = geom_of<T>(s);
   s->prof.begin(KID_FUSED, st);
-  int rc = launch_fused<T, MODE>(G, s->x[in], s->ubar[in], s->vbar[in], s->x[0], out,
+  int rc = launch_fused<T, MODE, TERMS>(G, s->x[in], s->ubar[in], s->vbar[in], s->x[0], out,
                                  outb >= 0 ? s->ubar[outb] : nullptr, outb >= 0 ? s->vbar[outb] : nullptr,
                                  s->ubar[0], s->vbar[0], cdt, s->err, st);
   s->prof.end(st);
@@ -439,6 +440,31 @@ int run_steps(agcm_state* s, int nsteps, double dt, cudaStream_t st) {
     if ((rc = fused_stage<T, 1>(s, 0, s->x[1], 1, 0.5 * dt, st))) return rc;
     if ((rc = fused_stage<T, 2>(s, 1, s->x[2], 2, 0.5 * dt, st))) return rc;
     if ((rc = fused_stage<T, 2>(s, 2, s->x[0], 0, dt, st))) return rc;
+  }
+  return AGCM_OK;
+}
+
+// Split stepping (Sec. "Optimizations": A_F is called 3 M times and L_F 3
+// times per step, reading the labels as A = adaptation, L = advection): per
+// step, msub three-stage steps of the adaptation terms with dt/msub, then one
+// three-stage step of the advection terms with dt.
+template <class T, int TERMS>
+int three_stage(agcm_state* s, double dt, cudaStream_t st) {
+  int rc;
+  if ((rc = fused_stage<T, 1, TERMS>(s, 0, s->x[1], 1, 0.5 * dt, st))) return rc;
+  if ((rc = fused_stage<T, 2, TERMS>(s, 1, s->x[2], 2, 0.5 * dt, st))) return rc;
+  return fused_stage<T, 2, TERMS>(s, 2, s->x[0], 0, dt, st);
+}
+
+template <class T>
+int run_steps_split(agcm_state* s, int nsteps, double dt, int msub, cudaStream_t st) {
+  if (sizeof(T) == 4) s->bar_valid = false;
+  int rc = ensure_bar<T>(s, st);
+  if (rc) return rc;
+  for (int n = 0; n < nsteps; ++n) {
+    for (int m = 0; m < msub; ++m)
+      if ((rc = three_stage<T, 2>(s, dt / msub, st))) return rc;
+    if ((rc = three_stage<T, 1>(s, dt, st))) return rc;
   }
   return AGCM_OK;
 }
@@ -723,6 +749,29 @@ int agcm_step(agcm_state_t* s, int nsteps, double dt, void* stream) {
   if (nsteps == 0) return AGCM_OK;
   cudaStream_t st = as_stream(stream);
   return s->prec == AGCM_FP64 ? run_steps<double>(s, nsteps, dt, st) : run_steps<float>(s, nsteps, dt, st);
+}
+
+int agcm_step_split(agcm_state_t* s, int nsteps, double dt, int msub, void* stream) {
+  if (!s || nsteps < 0 || msub < 1 || msub > 64 || !std::isfinite(dt)) return fail(AGCM_EINVAL, "bad argument");
+  if (nsteps == 0) return AGCM_OK;
+  cudaStream_t st = as_stream(stream);
+  return s->prec == AGCM_FP64 ? run_steps_split<double>(s, nsteps, dt, msub, st)
+                              : run_steps_split<float>(s, nsteps, dt, msub, st);
+}
+
+int agcm_grid_dt_split(const agcm_grid_t* g, double umax, double* dt, int* msub) {
+  if (!g || !dt || !msub || !(umax > 0.0)) return fail(AGCM_EINVAL, "bad argument");
+  // adaptation alone: the gravity-wave bound (c_max only); advection alone:
+  // the same wavenumber bound with the flow speed umax only
+  double dt_grav = 0.0;
+  int rc = agcm_grid_dt(g, 0.0, &dt_grav);
+  if (rc) return rc;
+  const double kx = 2.0 / (kA * std::sqrt(0.5) * g->dlam), ky = 2.0 / (kA * g->dth);
+  const double dtl = 1.6 / (umax * std::sqrt(kx * kx + ky * ky));
+  *dt = dtl;
+  *msub = (int)std::ceil(dtl / dt_grav - 1e-9);
+  if (*msub < 1) *msub = 1;
+  return AGCM_OK;
 }
 
 int agcm_tendency(agcm_state_t* s, void* tU, void* tV, void* tPhi, void* tpi, void* stream) {

@@ -156,7 +156,10 @@ __device__ __forceinline__ void tile_issue(const TileCtx<T>& t, const Geom<T>& g
 // Ubar_b/Vbar_b: vertical means of the base state (FP32 path, MODE > 0): the
 // output's means are base + sum_k dsigma_k (out_k - base_k), the increments
 // being exact differences of stored floats, so no FP64 work runs per level.
-template <class T, int MODE, bool TILE>
+// TERMS selects the term groups of Eq. 2: 1 = advection L (skew flux form,
+// vertical advection), 2 = adaptation A (pressure gradient, Coriolis pair,
+// Omega~ conversion, dpi/dt), 3 = both (the unsplit step).
+template <class T, int MODE, bool TILE, int TERMS = 3>
 __device__ __forceinline__ void fused_column(
     const Geom<T>& g, const int i, const int j, const T* __restrict__ U, const T* __restrict__ V,
     const T* __restrict__ Phi, const T* __restrict__ pi, const double* __restrict__ Ubar,
@@ -164,6 +167,7 @@ __device__ __forceinline__ void fused_column(
     T* pio, double* Ubar_o, double* Vbar_o, const double* Ubar_b, const double* Vbar_b, const T cdt,
     const TileCtx<T>* tc = nullptr, const bool active = true) {
   const int I = g.I, J = g.J, K = g.K;
+  constexpr bool ADV = (TERMS & 1) != 0, ADA = (TERMS & 2) != 0;
   const bool hasS = j < J - 1;   // V row j exists, scalar row j+1 exists
   const bool hasN = j > 0;       // V row j-1 exists
   const bool hasSS = j + 1 < J - 1;  // V row j+1 exists
@@ -272,10 +276,10 @@ __device__ __forceinline__ void fused_column(
              (double)rdys;
   if (active) {
     if (MODE == 0)
-      pio[rj + i] = (T)(-Cc);
+      pio[rj + i] = ADA ? (T)(-Cc) : T(0);
     else {
       const double pb = (MODE == 1) ? (double)pi[rj + i] : (double)pib[rj + i];
-      pio[rj + i] = (T)(pb - (double)cdt * Cc);
+      pio[rj + i] = ADA ? (T)(pb - (double)cdt * Cc) : (T)pb;
     }
   }
   const T Cf = (T)Cc, Cpf = (T)Cp, Csf = (T)Cs;
@@ -395,7 +399,7 @@ __device__ __forceinline__ void fused_column(
         if (hasS) hor += yvj * Ftc * Phs * rPs;
         if (hasN) hor -= yvjm * Ftn * Phn * rPn;
         const T X = -(b * rPc) * (Hkk * D + hkr * (Cf - SD));
-        nPPh = X - (hor * r2A + Wb * GsB * r2dsk) * rPc;
+        nPPh = (ADA ? X : T(0)) - (ADV ? (hor * r2A + Wb * GsB * r2dsk) * rPc : T(0));
       }
       // ---- U cell
       Guc = Uc * rPuc;
@@ -412,7 +416,7 @@ __device__ __forceinline__ void fused_column(
         const T pgf = Puc * dpsi * rdx;
         const T fs = f0 + Guc * cota;
         const T vs = Vn + Vnp + Vc + Vp;
-        nPU = -(hor * r2A + WuB * GuB * r2dsk) * rPuc - pgf - T(0.25) * fs * vs;
+        nPU = (ADV ? -(hor * r2A + WuB * GuB * r2dsk) * rPuc : T(0)) - (ADA ? pgf + T(0.25) * fs * vs : T(0));
       }
       // ---- V cell
       if (hasS) {
@@ -431,15 +435,15 @@ __device__ __forceinline__ void fused_column(
         const T pgf = Pvc * dpsi * rady;
         const T cor = cn * ((f0 + Um * rPum * cota) * Um + (f0 + Uc * rPuc * cota) * Uc) +
                       cs * ((f0s + Usm * rPusm * cotas) * Usm + (f0s + Us * rPus * cotas) * Us);
-        nPV = -(hor * r2Av + WvB * GvB * r2dsk) * rPvc - pgf + cor;
+        nPV = (ADV ? -(hor * r2Av + WvB * GvB * r2dsk) * rPvc : T(0)) + (ADA ? cor - pgf : T(0));
       }
     }
     // ---- complete level k+1 with its top-face vertical term (needs G_k) and write it
     if (k + 1 <= K - 1) {
       const int kk = k + 1;
       const T r2dsk1 = p_r2;
-      const T TPh = PPh + Wb * Gsc * r2dsk1 * rPc;
-      const T TU = PU + T(0.5) * (Wb + Wbp) * Guc * r2dsk1 * rPuc;
+      const T TPh = PPh + (ADV ? Wb * Gsc * r2dsk1 * rPc : T(0));
+      const T TU = PU + (ADV ? T(0.5) * (Wb + Wbp) * Guc * r2dsk1 * rPuc : T(0));
       const size_t o = (size_t)kk * plane + rj + i;
       const T bPh = MODE == 0 ? T(0) : pbPh, bU = MODE == 0 ? T(0) : pbU;
       const T oPh = bPh + cdt * TPh, oU = bU + cdt * TU;
@@ -453,7 +457,7 @@ __device__ __forceinline__ void fused_column(
         ubar += p_dsd * (double)oU;
       }
       if (hasS) {
-        const T TV = PV + T(0.5) * (Wb + Wbs) * Gvc * r2dsk1 * rPvc;
+        const T TV = PV + (ADV ? T(0.5) * (Wb + Wbs) * Gvc * r2dsk1 * rPvc : T(0));
         const size_t ov = (size_t)kk * vplane + rj + i;
         const T bV = MODE == 0 ? T(0) : pbV;
         const T oV = bV + cdt * TV;
@@ -495,7 +499,7 @@ __device__ __forceinline__ void fused_column(
 // global memory (the row index is warp-uniform, so row tables sit in uniform
 // registers).  BY = kTileY: a 32 x 4 tile whose levels are staged in shared
 // memory by the TMA bulk-copy engine (global loads where the halo is too wide).
-template <class T, int MODE, int BY>
+template <class T, int MODE, int BY, int TERMS = 3>
 __global__ void __launch_bounds__(kTileX* BY, BY == 1 ? (sizeof(T) == 4 ? AGCM_FUSED_MINB : AGCM_FUSED_MINB64)
                                                       : (sizeof(T) == 4 ? AGCM_TILE_MINB : 2))
     k_fused_stage(Geom<T> g, const T* __restrict__ U, const T* __restrict__ V, const T* __restrict__ Phi,
@@ -507,7 +511,7 @@ __global__ void __launch_bounds__(kTileX* BY, BY == 1 ? (sizeof(T) == 4 ? AGCM_F
   if (BY == 1) {
     const int i = blockIdx.x * kTileX + tx, j = blockIdx.y;
     if (i < g.I)
-      fused_column<T, MODE, false>(g, i, j, U, V, Phi, pi, Ubar, Vbar, Ub, Vb, Phib, pib, Uo, Vo, Phio, pio, Ubar_o,
+      fused_column<T, MODE, false, TERMS>(g, i, j, U, V, Phi, pi, Ubar, Vbar, Ub, Vb, Phib, pib, Uo, Vo, Phio, pio, Ubar_o,
                                    Vbar_o, Ubar_b, Vbar_b, cdt);
     return;
   }
@@ -525,7 +529,7 @@ __global__ void __launch_bounds__(kTileX* BY, BY == 1 ? (sizeof(T) == 4 ? AGCM_F
   const bool tile = tile_enable && H <= kHaloMax && (g.I % 4) == 0 && kTileX + 2 * H <= g.I;
   if (!tile) {
     if (active)
-      fused_column<T, MODE, false>(g, i, j, U, V, Phi, pi, Ubar, Vbar, Ub, Vb, Phib, pib, Uo, Vo, Phio, pio, Ubar_o,
+      fused_column<T, MODE, false, TERMS>(g, i, j, U, V, Phi, pi, Ubar, Vbar, Ub, Vb, Phib, pib, Uo, Vo, Phio, pio, Ubar_o,
                                    Vbar_o, Ubar_b, Vbar_b, cdt);
     return;
   }
@@ -552,7 +556,7 @@ __global__ void __launch_bounds__(kTileX* BY, BY == 1 ? (sizeof(T) == 4 ? AGCM_F
     mbar_fence_init();
   }
   __syncthreads();
-  fused_column<T, MODE, true>(g, min(i, g.I - 1), min(j, g.J - 1), U, V, Phi, pi, Ubar, Vbar, Ub, Vb, Phib, pib,
+  fused_column<T, MODE, true, TERMS>(g, min(i, g.I - 1), min(j, g.J - 1), U, V, Phi, pi, Ubar, Vbar, Ub, Vb, Phib, pib,
                               Uo, Vo, Phio, pio, Ubar_o, Vbar_o, Ubar_b, Vbar_b, cdt, &t, active);
 }
 

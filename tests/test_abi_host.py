@@ -96,3 +96,15 @@ def test_cfl_dt_matches_column_eigenproblem(L):
         dl, dth = 2 * math.pi / I, math.pi / J
         want = 1.6 / ((cmax + 100.0) * math.hypot(2 / (a * math.cos(math.pi / 4) * dl), 2 / (a * dth)))
         assert abs(g.dt(100.0) / want - 1) < 1e-10
+
+
+def test_split_dt_rule(L):
+    """Advective dt from the flow speed alone, and enough adaptation sub-steps
+    for each to respect the gravity-wave dt."""
+    g = agcm.Grid(256, 128, 30)
+    dt, m = g.dt_split(100.0)
+    a = 6.371e6
+    dl, dth = 2 * math.pi / 256, math.pi / 128
+    want = 1.6 / (100.0 * math.hypot(2 / (a * math.cos(math.pi / 4) * dl), 2 / (a * dth)))
+    assert abs(dt / want - 1) < 1e-12
+    assert dt / m <= g.dt(0.0) * (1 + 1e-12) and dt / (m - 1) > g.dt(0.0)

@@ -220,3 +220,31 @@ def test_allocation_failure_is_reported_and_leaks_nothing():
         agcm.use_torch_allocator()
     s = agcm.State(g, agcm.AGCM_FP64)
     s.close()
+
+
+def _oracle_split(o, st, dt, msub, nsteps):
+    """The split step from the oracle's term groups: msub three-stage steps of
+    the adaptation terms with dt/msub, then one of the advection terms with dt."""
+    ada = oracle.TERM_COR | oracle.TERM_PGF_PI | oracle.TERM_PGF_PHI
+    x = {f: st[f] for f in FIELDS}
+    for _ in range(nsteps):
+        x = o.step(x, dt / msub, msub, terms=ada)
+        x = o.step(x, dt, 1, terms=oracle.TERM_ADV)
+    return x
+
+
+@pytest.mark.parametrize("case", [(37, 23, 7, "random", {}), (128, 64, 8, "rh4", {}), (256, 128, 30, "jet", {})],
+                         ids=lambda c: f"{c[0]}x{c[1]}x{c[2]}")
+def test_split_step_matches_oracle(case):
+    g, o, st = make_case(*case)
+    dt, msub = g.dt_split(100.0)
+    assert msub >= 2
+    ref = _oracle_split(o, st, dt, msub, 2)
+    for prec, tol in ((agcm.AGCM_FP64, 1e-11), (agcm.AGCM_FP32, 1e-5)):
+        s = agcm.State(g, prec)
+        s.load(st)
+        s.step_split(2, dt, msub)
+        out = to_np(s.store())
+        for f in FIELDS:
+            assert rel_err(out[f], ref[f]) <= tol, (prec, f, rel_err(out[f], ref[f]))
+        s.close()

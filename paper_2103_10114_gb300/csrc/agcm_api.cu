@@ -243,10 +243,11 @@ int upload_geom(agcm_grid* g, int p) {
     cn[j] = 0.25 * g->A[j] / g->Av[j];
     cs[j] = 0.25 * g->A[j + 1] / g->Av[j];
   }
-  std::vector<double> r2ds(K), hk_rds(K);
+  std::vector<double> r2ds(K), hk_rds(K), oms(K);
   for (int k = 0; k < K; ++k) {
     r2ds[k] = 0.5 / g->ds[k];
     hk_rds[k] = g->hk[k] / g->ds[k];
+    oms[k] = 1.0 - g->sh[k];
   }
   std::vector<double> rt0pit((size_t)J * I);
   for (size_t n = 0; n < rt0pit.size(); ++n) rt0pit[n] = kR * kT0 / g->pit[n];
@@ -262,7 +263,7 @@ int upload_geom(agcm_grid* g, int p) {
          o_cn = putT(cn.empty() ? std::vector<double>{0} : cn),
          o_cs = putT(cs.empty() ? std::vector<double>{0} : cs);
   size_t o_ds = putT(g->ds), o_r2ds = putT(r2ds), o_hk = putT(g->hk), o_Hkk = putT(g->Hkk),
-         o_hkr = putT(hk_rds), o_dsd = putD(g->ds), o_shd = putD(g->sh), o_Ad = putD(g->A),
+         o_hkr = putT(hk_rds), o_oms = putT(oms), o_dsd = putD(g->ds), o_shd = putD(g->sh), o_Ad = putD(g->A),
          o_Avd = putD(g->Av.empty() ? std::vector<double>{0} : g->Av);
   size_t o_rt0 = putT(rt0pit), o_pit = putT(g->pit);
 
@@ -294,6 +295,7 @@ int upload_geom(agcm_grid* g, int p) {
   G.hk = (const T*)(base + o_hk);
   G.Hkk = (const T*)(base + o_Hkk);
   G.hk_rds = (const T*)(base + o_hkr);
+  G.oms = (const T*)(base + o_oms);
   G.dsd = (const double*)(base + o_dsd);
   G.shd = (const double*)(base + o_shd);
   G.Ad = (const double*)(base + o_Ad);
@@ -972,8 +974,8 @@ constexpr size_t kOffRawLev = kOffRaw + 6 * kRowB;   // sh ds Hkk hk (double)
 constexpr size_t kOffPitRaw = kOffRawLev + 4 * kLevB;  // pi~ (double)
 constexpr size_t kOffInt = kOffPitRaw + kColB;       // Mu Mv (int)
 constexpr size_t kOffRowT = kOffInt + 2 * kRowB;     // 12 typed row arrays
-constexpr size_t kOffLevT = kOffRowT + 12 * kRowB;   // 5 typed level arrays
-constexpr size_t kOffColT = kOffLevT + 5 * kLevB;    // pit, rt0pit (typed)
+constexpr size_t kOffLevT = kOffRowT + 12 * kRowB;   // 6 typed level arrays
+constexpr size_t kOffColT = kOffLevT + 6 * kLevB;    // pit, rt0pit (typed)
 constexpr size_t kOffBar = kOffColT + 2 * kColB;     // Ubar, Vbar (double)
 constexpr size_t kStaticBytes = kOffBar + 2 * kColB; // about 11 MB
 
@@ -1026,6 +1028,7 @@ __global__ void k_static_geom(int I, int J, int K, const double* raw, const doub
       levT[2 * levStride + k] = (T)hk[k];
       levT[3 * levStride + k] = (T)rawlev[2 * levStride + k];
       levT[4 * levStride + k] = (T)(hk[k] / ds[k]);
+      levT[5 * levStride + k] = (T)(1.0 - rawlev[k]);
     }
     colT[n] = (T)pitraw[n];
     colT[colStride + n] = (T)(kR * kT0 / pitraw[n]);
@@ -1069,6 +1072,7 @@ int tendency_static(const agcm_grid* g, char* base, const void* U, const void* V
   G.zfv = rowT + 8 * rS; G.r2Av = rowT + 9 * rS; G.cn = rowT + 10 * rS; G.cs = rowT + 11 * rS;
   G.ds = levT + 0 * lS; G.r2ds = levT + 1 * lS; G.hk = levT + 2 * lS; G.Hkk = levT + 3 * lS;
   G.hk_rds = levT + 4 * lS;
+  G.oms = levT + 5 * lS;
   G.dsd = rawlev + 1 * lS;
   G.shd = rawlev + 0 * lS;
   G.Ad = raw + 3 * rS;

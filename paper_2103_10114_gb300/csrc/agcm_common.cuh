@@ -36,6 +36,7 @@ struct Geom {
   const T* hk;      // H[k'][k'] off-diagonal weight ln(sh_{k+1}/sh_k), hk[0] = 0 (K)
   const T* Hkk;     // diagonal ln(sh_{k+1}/sigma_k) (K)
   const T* hk_rds;  // hk / dsigma_k (K)
+  const T* oms;     // 1 - sigma_hat_k (K): W_k = SD_k - (1 - sigma_hat_k) C
   const double* dsd;  // dsigma_k in FP64 (column integral of the divergence)
   const double* shd;  // half levels sigma_hat_h in FP64 (K+1)
   const double* Ad;   // A_j in FP64 (J)     (diagnostics)

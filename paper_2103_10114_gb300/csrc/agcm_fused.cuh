@@ -304,7 +304,7 @@ __device__ __forceinline__ void fused_column(
   // its level is computed, and the base state of a level one iteration before
   // that level is completed and written
   T q_ds = g.ds[K - 1], q_H = g.Hkk[K - 1], q_hk = g.hk[K - 1], q_hr = g.hk_rds[K - 1], q_r2 = g.r2ds[K - 1];
-  T q_om = T(1.0 - g.shd[K - 1]);
+  T q_om = g.oms[K - 1];
   double q_dsd = g.dsd[K - 1];
   T p_r2 = 0, p_ds = 0;   // level below: 1/(2 dsigma), dsigma
   double p_dsd = 0.0;
@@ -349,7 +349,7 @@ __device__ __forceinline__ void fused_column(
         q_hk = g.hk[k - 1];
         q_hr = g.hk_rds[k - 1];
         q_r2 = g.r2ds[k - 1];
-        q_om = T(1.0 - g.shd[k - 1]);
+        q_om = g.oms[k - 1];
         q_dsd = g.dsd[k - 1];
       }
       // loads

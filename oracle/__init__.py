@@ -60,6 +60,9 @@ def lib():
         _lib.orc_tendency_jvp.argtypes = [vp] + [d] * 12 + [ctypes.c_uint]
         _lib.orc_step_jvp.argtypes = [vp] + [d] * 8 + [ctypes.c_double, ctypes.c_int, ctypes.c_uint]
         _lib.orc_diagnostics.argtypes = [vp] + [d] * 5
+        _lib.orc_filter_band.restype = ctypes.c_int
+        _lib.orc_filter_band.argtypes = [ctypes.c_double]
+        _lib.orc_filter.argtypes = [vp] + [d] * 4 + [ctypes.c_double]
     return _lib
 
 
@@ -79,6 +82,11 @@ def leap_ratio(theta: float, dlam: float) -> float:
 def zonal_dx(theta: float, dlam: float) -> float:
     """Zonal grid size a sin(theta) dlam in metres."""
     return lib().orc_zonal_dx(theta, dlam)
+
+
+def filter_band(colat: float) -> int:
+    """0: none, 1: two-grid-wave removal (|lat| < 38), 2: 3-point (38..70)."""
+    return lib().orc_filter_band(colat)
 
 
 def leap_table(nlon: int, nlat: int):
@@ -169,6 +177,12 @@ class Oracle:
         lib().orc_step_jvp(self._h, *[_dp(a) for a in x], *[_dp(a) for a in dx], float(dt),
                            int(nsteps), terms)
         return dict(zip(FIELDS, x)), dict(zip(FIELDS, dx))
+
+    def filter(self, st, r=0.25):
+        """Low-latitude filters (Table "Conventional Filtering scheme"), a new state."""
+        x = [a.copy() for a in self._in(st)]
+        lib().orc_filter(self._h, *[_dp(a) for a in x], float(r))
+        return dict(zip(FIELDS, x))
 
     def diagnostics(self, st):
         x = self._in(st)

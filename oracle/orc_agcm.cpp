@@ -400,6 +400,35 @@ void step(const Grid& g, T* U, T* V, T* Ph, T* pi, double dt, int nsteps, unsign
 
 }  // namespace
 
+// ---- low-latitude filters (Table "Conventional Filtering scheme") ---------
+// Band by latitude phi = 90deg - colatitude: 1 = "simplified" filter for
+// |phi| < 38deg, read as removing the two-grid-interval zonal wave exactly
+// (the printed sum is garbled: F_x - (-1)^x (1/I) sum_x' (-1)^x' F_x');
+// 2 = the 3-point operator F_x + r (F_{x-1} - 2 F_x + F_{x+1}) for
+// 38deg <= |phi| <= 70deg; 0 = none (the leap format covers |phi| > 70deg).
+int filter_band(double colat) {
+  const double lat = std::fabs(90.0 - colat * 180.0 / kPi);
+  if (lat < 38.0) return 1;
+  if (lat <= 70.0) return 2;
+  return 0;
+}
+
+void filter_row(double* F, int I, int band, double r) {
+  if (band == 1) {
+    if (I % 2 != 0) return;  // no two-grid wave on an odd circle
+    double alt = 0.0;
+    for (int x = 0; x < I; ++x) alt += (x % 2 == 0 ? 1.0 : -1.0) * F[x];
+    const double a = alt / I;
+    for (int x = 0; x < I; ++x) F[x] -= (x % 2 == 0 ? 1.0 : -1.0) * a;
+  } else if (band == 2) {
+    std::vector<double> old(F, F + I);
+    for (int x = 0; x < I; ++x) {
+      const double l = old[(x - 1 + I) % I], c = old[x], rr = old[(x + 1) % I];
+      F[x] = c + r * (l - 2.0 * c + rr);
+    }
+  }
+}
+
 // ======================= C interface for the tests =========================
 extern "C" {
 
@@ -518,6 +547,27 @@ void orc_step_jvp(void* h, double* U, double* V, double* Ph, double* pi, double*
   pack(U, dU, n3, xU); pack(V, dV, nv, xV); pack(Ph, dPh, n3, xP); pack(pi, dpi, n2, xp);
   step<Dual>(g, xU.data(), xV.data(), xP.data(), xp.data(), dt, nsteps, terms);
   unpack(xU, U, dU); unpack(xV, V, dV); unpack(xP, Ph, dPh); unpack(xp, pi, dpi);
+}
+
+int orc_filter_band(double colat) { return filter_band(colat); }
+
+// Apply the low-latitude filters in place to every row of U, Phi, pi (scalar
+// rows) and V (V rows), each row by its own latitude band.
+void orc_filter(void* h, double* U, double* V, double* Ph, double* pi, double r) {
+  const Grid& g = *static_cast<Grid*>(h);
+  const int I = g.I, J = g.J, K = g.K;
+  for (int j = 0; j < J; ++j) {
+    const int band = filter_band((j + 0.5) * g.dth);
+    for (int k = 0; k < K; ++k) {
+      filter_row(U + ((size_t)k * J + j) * I, I, band, r);
+      filter_row(Ph + ((size_t)k * J + j) * I, I, band, r);
+    }
+    filter_row(pi + (size_t)j * I, I, band, r);
+  }
+  for (int j = 0; j + 1 < J; ++j) {
+    const int band = filter_band((j + 1.0) * g.dth);
+    for (int k = 0; k < K; ++k) filter_row(V + ((size_t)k * (J - 1) + j) * I, I, band, r);
+  }
 }
 
 // a11: out[0] mass = sum A_j (pi~ + pi) [p0 m^2]; out[1] kinetic, out[2]

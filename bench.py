@@ -15,6 +15,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -181,7 +182,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
-    ap.add_argument("--only", choices=["adjoint", "ensemble", "fp64", "split"],
+    ap.add_argument("--only", choices=["adjoint", "ensemble", "fp64", "split", "filter"],
                     help="measure one form alone and print its JSON (for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -307,6 +308,8 @@ def run_only(form):
         out = measure_ensemble(agcm, inputs, torch, steps=3, per_member=False)
     elif form == "split":
         out = measure_split(agcm, inputs, torch, steps=3)
+    elif form == "filter":
+        out = measure_filter(agcm, inputs, torch, reps=3)
     else:
         I, J, K = WORKLOAD
         st = inputs.baroclinic_jet(I, J, K, seed=6, noise=1e-2, terrain_seed=2)
@@ -364,6 +367,10 @@ def measure_forms(agcm, inputs, torch, steps=5):
     except Exception as e:
         out["split_1440x720x30"] = {"error": repr(e)}
     try:
+        out["filter_1440x720x30"] = measure_filter(agcm, inputs, torch)
+    except Exception as e:
+        out["filter_1440x720x30"] = {"error": repr(e)}
+    try:
         out["ensemble_64"] = measure_ensemble(agcm, inputs, torch)
     except Exception as e:  # reported, not hidden
         out["ensemble_64"] = {"error": repr(e)}
@@ -391,6 +398,42 @@ def measure_split(agcm, inputs, torch, steps=5):
            "bytes_per_point_step": words * 4,
            "hbm_frac_step": pts / (ms / 1e3) * words * 4 / (peaks()[0] * 1e9),
            "sypd_equiv": pts / (ms / 1e3) / pts * dt / 365.0,
+           "finite": bool(s.diagnostics()["finite"])}
+    s.close()
+    return res
+
+
+def measure_filter(agcm, inputs, torch, reps=20):
+    """The low-latitude filters at 1440x720x30 FP32: the filter alone (bytes:
+    one read and one write of every row it changes) and a step followed by the
+    filter."""
+    I, J, K = WORKLOAD
+    st = inputs.baroclinic_jet(I, J, K, seed=6, noise=1e-2, terrain_seed=2)
+    g = agcm.Grid(I, J, K, phis=st["phis"])
+    dt = g.dt(100.0)
+    s = agcm.State(g, agcm.AGCM_FP32)
+    s.load(st)
+    s.filter()
+    ms_f = _time(torch, s.filter, reps)
+    dth = math.pi / J
+
+    def changed(colat):  # rows the filter rewrites: |latitude| <= 70 degrees (nlon even)
+        return abs(90.0 - math.degrees(colat)) <= 70.0
+
+    nu = sum(1 for j in range(J) if changed((j + 0.5) * dth))
+    nv = sum(1 for j in range(J - 1) if changed((j + 1.0) * dth))
+    rows = (2 * K + 1) * nu + K * nv
+    bytes_ = rows * I * 4 * 2
+    s.step(1, dt)
+
+    def both():
+        s.step(1, dt)
+        s.filter()
+
+    ms_s = _time(torch, both, 5)
+    res = {"filter_ms": ms_f, "filter_gbs": bytes_ / (ms_f / 1e3) / 1e9,
+           "filter_hbm_frac": bytes_ / (ms_f / 1e3) / 1e9 / peaks()[0], "filtered_rows": rows,
+           "value": I * J * K / (ms_s / 1e3), "unit": "gp-steps/s (step + filter)", "ms_per_step": ms_s,
            "finite": bool(s.diagnostics()["finite"])}
     s.close()
     return res

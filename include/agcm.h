@@ -130,6 +130,17 @@ int agcm_state_store(const agcm_state_t* state, void* U, void* V, void* Phi, voi
 int agcm_step(agcm_state_t* state, int nsteps, double dt, void* stream);
 
 /*
+ * agcm_filter — the low-latitude filters the leap format keeps (Table
+ * "Conventional Filtering scheme"), applied in place to x_n, each zonal row by
+ * its latitude: |lat| < 38 deg removes the two-grid-interval wave (the
+ * printed sum read as that projection; skipped when nlon is odd);
+ * 38..70 deg applies F + r (F_{x-1} - 2F + F_{x+1}) with 0 < r <= 1/4 (the
+ * paper's r_j is not given; 1/4 removes the two-grid wave); poleward of 70
+ * deg nothing.  Every row sum is kept, so mass is kept.  Asynchronous.
+ */
+int agcm_filter(agcm_state_t* state, double r, void* stream);
+
+/*
  * agcm_step_split — split time stepping (Sec. "Optimizations": per step the
  * adaptation process is called 3*M times and the advection process 3 times;
  * reading the labels as A = adaptation, L = advection): each of the nsteps

@@ -77,6 +77,7 @@ SIGNATURES = {
     "agcm_step": (_i, [_vp, _i, _d, _vp]),
     "agcm_tendency": (_i, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "agcm_step_split": (_i, [_vp, _i, _d, _i, _vp]),
+    "agcm_filter": (_i, [_vp, _d, _vp]),
     "agcm_grid_dt_split": (_i, [_vp, _d, _pd, ctypes.POINTER(ctypes.c_int)]),
     "agcm_step_adjoint": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _d, _vp]),
     "agcm_diagnostics": (_i, [_vp, _vp, _vp]),
@@ -265,6 +266,9 @@ class State:
 
     def step(self, nsteps, dt, stream=None):
         check(lib().agcm_step(self._h, int(nsteps), float(dt), _stream_ptr(stream)))
+
+    def filter(self, r=0.25, stream=None):
+        check(lib().agcm_filter(self._h, float(r), _stream_ptr(stream)))
 
     def step_split(self, nsteps, dt, msub, stream=None):
         check(lib().agcm_step_split(self._h, int(nsteps), float(dt), int(msub), _stream_ptr(stream)))

@@ -22,6 +22,7 @@
 #include "agcm_adjoint.cuh"
 #include "agcm_diag.cuh"
 #include "agcm_ensemble.cuh"
+#include "agcm_filter.cuh"
 
 namespace {
 
@@ -121,11 +122,12 @@ enum KernelId : int {
   KID_ADJ_COLSTATE,
   KID_ADJ_AXPY,
   KID_ENSEMBLE,
+  KID_FILTER,
   KID_COUNT
 };
 static const char* const kKernelNames[KID_COUNT] = {
     "k_colstate", "k_column", "k_update", "k_fused_colsum", "k_fused_stage", "k_diag",
-    "k_adj_update", "k_adj_column", "k_adj_colstate", "k_adj_axpy", "k_ensemble"};
+    "k_adj_update", "k_adj_column", "k_adj_colstate", "k_adj_axpy", "k_ensemble", "k_filter"};
 
 struct Profiler {
   bool on = false;
@@ -249,6 +251,14 @@ int upload_geom(agcm_grid* g, int p) {
     hk_rds[k] = g->hk[k] / g->ds[k];
     oms[k] = 1.0 - g->sh[k];
   }
+  // low-latitude filter bands (Table "Conventional Filtering scheme")
+  auto band_of = [](double colat) {
+    const double lat = std::fabs(90.0 - colat * 180.0 / kPi);
+    return lat < 38.0 ? 1 : (lat <= 70.0 ? 2 : 0);
+  };
+  std::vector<int> bandU(J), bandV(std::max(JV, 1), 0);
+  for (int j = 0; j < J; ++j) bandU[j] = band_of((j + 0.5) * g->dth);
+  for (int j = 0; j < JV; ++j) bandV[j] = band_of((j + 1.0) * g->dth);
   std::vector<double> rt0pit((size_t)J * I);
   for (size_t n = 0; n < rt0pit.size(); ++n) rt0pit[n] = kR * kT0 / g->pit[n];
 
@@ -266,6 +276,7 @@ int upload_geom(agcm_grid* g, int p) {
          o_hkr = putT(hk_rds), o_oms = putT(oms), o_dsd = putD(g->ds), o_shd = putD(g->sh), o_Ad = putD(g->A),
          o_Avd = putD(g->Av.empty() ? std::vector<double>{0} : g->Av);
   size_t o_rt0 = putT(rt0pit), o_pit = putT(g->pit);
+  size_t o_bu = putI(bandU), o_bv = putI(bandV);
 
   void* d = dev_alloc(host.size());
   if (!d) return fail(AGCM_ENOMEM, "device allocation of %zu bytes for the grid tables failed", host.size());
@@ -296,6 +307,8 @@ int upload_geom(agcm_grid* g, int p) {
   G.Hkk = (const T*)(base + o_Hkk);
   G.hk_rds = (const T*)(base + o_hkr);
   G.oms = (const T*)(base + o_oms);
+  G.bandU = (const int*)(base + o_bu);
+  G.bandV = (const int*)(base + o_bv);
   G.dsd = (const double*)(base + o_dsd);
   G.shd = (const double*)(base + o_shd);
   G.Ad = (const double*)(base + o_Ad);
@@ -751,6 +764,29 @@ int agcm_step(agcm_state_t* s, int nsteps, double dt, void* stream) {
   if (nsteps == 0) return AGCM_OK;
   cudaStream_t st = as_stream(stream);
   return s->prec == AGCM_FP64 ? run_steps<double>(s, nsteps, dt, st) : run_steps<float>(s, nsteps, dt, st);
+}
+
+int agcm_filter(agcm_state_t* s, double r, void* stream) {
+  if (!s || !(r > 0.0) || r > 0.25) return fail(AGCM_EINVAL, "filter weight r must be in (0, 1/4]");
+  cudaStream_t st = as_stream(stream);
+  const agcm_grid* g = s->grid;
+  const int I = g->I, J = g->J, K = g->K;
+  auto run = [&](auto tag) -> int {
+    using T = decltype(tag);
+    const agcm::Geom<T>& G = geom_of<T>(s);
+    const size_t smem = (size_t)I * sizeof(T);
+    s->prof.begin(KID_FILTER, st);
+    agcm::k_filter<T><<<K * J, 256, smem, st>>>(G.bandU, (T*)s->x[0][0], I, J, K * J, (T)r);
+    agcm::k_filter<T><<<K * J, 256, smem, st>>>(G.bandU, (T*)s->x[0][2], I, J, K * J, (T)r);
+    if (J > 1) agcm::k_filter<T><<<K * (J - 1), 256, smem, st>>>(G.bandV, (T*)s->x[0][1], I, J - 1, K * (J - 1), (T)r);
+    agcm::k_filter<T><<<J, 256, smem, st>>>(G.bandU, (T*)s->x[0][3], I, J, J, (T)r);
+    s->prof.end(st);
+    CUDA_TRY(cudaGetLastError());
+    return AGCM_OK;
+  };
+  if ((size_t)I * 8 > 200 * 1024) return fail(AGCM_EINVAL, "nlon too large for the row filter");
+  s->bar_valid = false;  // the filtered state needs fresh vertical means
+  return s->prec == AGCM_FP64 ? run(double(0)) : run(float(0));
 }
 
 int agcm_step_split(agcm_state_t* s, int nsteps, double dt, int msub, void* stream) {

@@ -33,7 +33,7 @@ BYTES_PER_POINT_STEP = {4: 96, 8: 192}  # 24 words: stages read/write 6 + 9 + 9 
 # (profiles/), valid only while the kernel source is the one that was captured.
 NCU_TRAFFIC = {
     # kernel name: (sha1 of csrc/agcm_fused.cuh at capture time, bytes per launch, profile file)
-    "k_fused_stage": ("a39ed0e49796b5d68579fc889d88caf9f449a60d", 1078187605,
+    "k_fused_stage": ("c3e706169b73c2f492ce566441542579c37deeaa", 1072928768,
                       "profiles/fused_stage_1440x720x30_fp32.md"),
 }
 

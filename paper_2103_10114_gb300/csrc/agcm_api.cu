@@ -256,9 +256,18 @@ int upload_geom(agcm_grid* g, int p) {
     const double lat = std::fabs(90.0 - colat * 180.0 / kPi);
     return lat < 38.0 ? 1 : (lat <= 70.0 ? 2 : 0);
   };
-  std::vector<int> bandU(J), bandV(std::max(JV, 1), 0);
-  for (int j = 0; j < J; ++j) bandU[j] = band_of((j + 0.5) * g->dth);
-  for (int j = 0; j < JV; ++j) bandV[j] = band_of((j + 1.0) * g->dth);
+  std::vector<int> filtU, filtV;  // the two-grid removal needs an even nlon
+  for (int j = 0; j < J; ++j) {
+    const int bnd = band_of((j + 0.5) * g->dth);
+    if (bnd == 2 || (bnd == 1 && I % 2 == 0)) filtU.push_back(4 * j + bnd);
+  }
+  for (int j = 0; j < JV; ++j) {
+    const int bnd = band_of((j + 1.0) * g->dth);
+    if (bnd == 2 || (bnd == 1 && I % 2 == 0)) filtV.push_back(4 * j + bnd);
+  }
+  const int nfU = (int)filtU.size(), nfV = (int)filtV.size();
+  filtU.push_back(0);
+  filtV.push_back(0);
   std::vector<double> rt0pit((size_t)J * I);
   for (size_t n = 0; n < rt0pit.size(); ++n) rt0pit[n] = kR * kT0 / g->pit[n];
 
@@ -276,7 +285,7 @@ int upload_geom(agcm_grid* g, int p) {
          o_hkr = putT(hk_rds), o_oms = putT(oms), o_dsd = putD(g->ds), o_shd = putD(g->sh), o_Ad = putD(g->A),
          o_Avd = putD(g->Av.empty() ? std::vector<double>{0} : g->Av);
   size_t o_rt0 = putT(rt0pit), o_pit = putT(g->pit);
-  size_t o_bu = putI(bandU), o_bv = putI(bandV);
+  size_t o_bu = putI(filtU), o_bv = putI(filtV);
 
   void* d = dev_alloc(host.size());
   if (!d) return fail(AGCM_ENOMEM, "device allocation of %zu bytes for the grid tables failed", host.size());
@@ -307,8 +316,10 @@ int upload_geom(agcm_grid* g, int p) {
   G.Hkk = (const T*)(base + o_Hkk);
   G.hk_rds = (const T*)(base + o_hkr);
   G.oms = (const T*)(base + o_oms);
-  G.bandU = (const int*)(base + o_bu);
-  G.bandV = (const int*)(base + o_bv);
+  G.filtU = (const int*)(base + o_bu);
+  G.filtV = (const int*)(base + o_bv);
+  G.nfU = nfU;
+  G.nfV = nfV;
   G.dsd = (const double*)(base + o_dsd);
   G.shd = (const double*)(base + o_shd);
   G.Ad = (const double*)(base + o_Ad);
@@ -771,22 +782,43 @@ int agcm_filter(agcm_state_t* s, double r, void* stream) {
   cudaStream_t st = as_stream(stream);
   const agcm_grid* g = s->grid;
   const int I = g->I, J = g->J, K = g->K;
-  auto run = [&](auto tag) -> int {
+  auto run = [&](auto tag, auto vw) -> int {
     using T = decltype(tag);
+    constexpr int VW = decltype(vw)::value;
     const agcm::Geom<T>& G = geom_of<T>(s);
-    const size_t smem = (size_t)I * sizeof(T);
+    const long long items = (long long)(2 * K + 1) * G.nfU + (long long)K * G.nfV;
+    if (items == 0) return AGCM_OK;
+    const size_t row_bytes = ((size_t)I * sizeof(T) + 15) & ~size_t(15);
+    const int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (96 * 1024) / row_bytes));
+    const size_t smem = (size_t)wpb * row_bytes;
+    auto kern = agcm::k_filter<T, VW>;
+    CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int dev = 0, nsm = 0, occ = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, wpb * 32, smem));
+    const long long want = (items + wpb - 1) / wpb;
+    const unsigned grid = (unsigned)std::max<long long>(1, std::min<long long>(want, (long long)std::max(occ, 1) * nsm));
+    agcm::FiltArgs<T> a{(T*)s->x[0][0], (T*)s->x[0][1], (T*)s->x[0][2], (T*)s->x[0][3],
+                        G.filtU, G.filtV, G.nfU, G.nfV, I, J, K, (int)row_bytes, items, (T)r};
     s->prof.begin(KID_FILTER, st);
-    agcm::k_filter<T><<<K * J, 256, smem, st>>>(G.bandU, (T*)s->x[0][0], I, J, K * J, (T)r);
-    agcm::k_filter<T><<<K * J, 256, smem, st>>>(G.bandU, (T*)s->x[0][2], I, J, K * J, (T)r);
-    if (J > 1) agcm::k_filter<T><<<K * (J - 1), 256, smem, st>>>(G.bandV, (T*)s->x[0][1], I, J - 1, K * (J - 1), (T)r);
-    agcm::k_filter<T><<<J, 256, smem, st>>>(G.bandU, (T*)s->x[0][3], I, J, J, (T)r);
+    kern<<<grid, wpb * 32, smem, st>>>(a);
     s->prof.end(st);
     CUDA_TRY(cudaGetLastError());
     return AGCM_OK;
   };
-  if ((size_t)I * 8 > 200 * 1024) return fail(AGCM_EINVAL, "nlon too large for the row filter");
+  if ((size_t)I * 8 > 96 * 1024) return fail(AGCM_EINVAL, "nlon too large for the row filter");
   s->bar_valid = false;  // the filtered state needs fresh vertical means
-  return s->prec == AGCM_FP64 ? run(double(0)) : run(float(0));
+  using V1 = std::integral_constant<int, 1>;
+  using V2 = std::integral_constant<int, 2>;
+  using V4 = std::integral_constant<int, 4>;
+  auto aligned = [&](size_t a) {  // vector rows need every field base on the vector size
+    for (int f = 0; f < 4; ++f)
+      if ((uintptr_t)s->x[0][f] % a) return false;
+    return true;
+  };
+  if (s->prec == AGCM_FP64) return I % 2 == 0 && aligned(16) ? run(double(0), V2{}) : run(double(0), V1{});
+  return I % 4 == 0 && aligned(16) ? run(float(0), V4{}) : run(float(0), V1{});
 }
 
 int agcm_step_split(agcm_state_t* s, int nsteps, double dt, int msub, void* stream) {

@@ -37,8 +37,10 @@ struct Geom {
   const T* Hkk;     // diagonal ln(sh_{k+1}/sigma_k) (K)
   const T* hk_rds;  // hk / dsigma_k (K)
   const T* oms;     // 1 - sigma_hat_k (K): W_k = SD_k - (1 - sigma_hat_k) C
-  const int* bandU; // low-latitude filter band of each scalar/U row (J): 0 none, 1 two-grid, 2 3-point
-  const int* bandV; // the same for the V rows (J-1)
+  // rows the low-latitude filter changes, entry 4 j + band (1 two-grid, 2 3-point)
+  const int* filtU; // scalar / U rows
+  const int* filtV; // V rows
+  int nfU, nfV;
   const double* dsd;  // dsigma_k in FP64 (column integral of the divergence)
   const double* shd;  // half levels sigma_hat_h in FP64 (K+1)
   const double* Ad;   // A_j in FP64 (J)     (diagnostics)

@@ -37,6 +37,16 @@ NCU_TRAFFIC = {
                       "profiles/fused_stage_1440x720x30_fp32.md"),
 }
 
+# Instruction counters of the dominant kernel (ncu, 720x360x30 FP32, one launch
+# of each stage kind, averaged over the three stages), valid while the kernel
+# source is the one that was captured: FP32 flops per point and stage
+# (fadd + fmul + 2 ffma), thread instructions per point, warp instructions
+# issued per point.
+NCU_OPS = {
+    "k_fused_stage": ("c3e706169b73c2f492ce566441542579c37deeaa", 228.8, 528.4, 16.9,
+                      "profiles/fused_stage_ops_720x360x30_fp32.md"),
+}
+
 
 def kernel_source_hash():
     import hashlib
@@ -182,7 +192,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
-    ap.add_argument("--only", choices=["adjoint", "ensemble", "fp64", "split", "filter"],
+    ap.add_argument("--only", choices=["adjoint", "ensemble", "fp64", "fp32_720", "split", "filter"],
                     help="measure one form alone and print its JSON (for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -262,6 +272,22 @@ def main():
     rec = NCU_TRAFFIC.get(name)
     if rec and rec[0] == kernel_source_hash():
         traffic, traffic_src = rec[1], rec[2]
+    compute = None
+    orec = NCU_OPS.get(name)
+    if orec and orec[0] == kernel_source_hash():
+        nsm = torch.cuda.get_device_properties(0).multi_processor_count
+        fmax = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"]) \
+            if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 2070.0
+        launch_s = kms / kn / 1e3
+        fp32 = orec[1] * pts / launch_s / 1e12
+        fp32_peak = nsm * 128 * 2 * fmax * 1e6 / 1e12
+        issue = orec[3] * pts / launch_s
+        issue_peak = nsm * 4 * fmax * 1e6
+        compute = {"fp32_flops_per_point_stage": orec[1], "thread_inst_per_point_stage": orec[2],
+                   "fp32_tflops": fp32, "fp32_peak_tflops": fp32_peak, "fp32_frac": fp32 / fp32_peak,
+                   "warp_inst_per_point_stage": orec[3], "issue_frac": issue / issue_peak,
+                   "peak_note": f"{nsm} SMs x 128 FP32 lanes x 2 x {fmax:.0f} MHz; issue: 4 warp-inst/SM/cycle",
+                   "source": orec[4]}
     launches = sum(n for _, n in prof.values())
     line = {
         "metric": "grid-point-steps/s", "value": value, "unit": "gp-steps/s", "n_gpus": world,
@@ -275,6 +301,7 @@ def main():
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic, "peak_kind": peak_kind,
                      "traffic_source": traffic_src, "bytes_per_launch": stage_bytes, "avg_launch_ms": kms / kn,
                      "note": "peak = measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},
+        "compute": compute,
         "kernels": {k: {"ms_total": v[0], "launches": v[1], "share": v[0] / sum(x[0] for x in prof.values())}
                     for k, v in prof.items()},
         "e2e": {"value": e2e, "unit": "gp-steps/s", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
@@ -310,11 +337,11 @@ def run_only(form):
         out = measure_split(agcm, inputs, torch, steps=3)
     elif form == "filter":
         out = measure_filter(agcm, inputs, torch, reps=3)
-    else:
-        I, J, K = WORKLOAD
+    else:  # fp64: the plain FP64 step at the bench size; fp32_720: FP32 at 720x360x30
+        I, J, K = WORKLOAD if form == "fp64" else (720, 360, 30)
         st = inputs.baroclinic_jet(I, J, K, seed=6, noise=1e-2, terrain_seed=2)
         g = agcm.Grid(I, J, K, phis=st["phis"])
-        s = agcm.State(g, agcm.AGCM_FP64)
+        s = agcm.State(g, agcm.AGCM_FP64 if form == "fp64" else agcm.AGCM_FP32)
         s.load(st)
         s.step(1, g.dt(100.0))
         ms = _time(torch, lambda: s.step(2, g.dt(100.0)), 1) / 2

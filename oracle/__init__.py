@@ -63,6 +63,7 @@ def lib():
         _lib.orc_filter_band.restype = ctypes.c_int
         _lib.orc_filter_band.argtypes = [ctypes.c_double]
         _lib.orc_filter.argtypes = [vp] + [d] * 4 + [ctypes.c_double]
+        _lib.orc_tendency_opcount.argtypes = [vp] + [d] * 8 + [ctypes.c_uint, ctypes.POINTER(ctypes.c_ulonglong)]
     return _lib
 
 
@@ -157,6 +158,16 @@ class Oracle:
         t = self.zeros()
         lib().orc_tendency(self._h, *[_dp(a) for a in x], *[_dp(t[f]) for f in FIELDS], terms)
         return t
+
+    def tendency_opcount(self, st, terms=TERM_ALL):
+        """The tendency evaluated through the counting type: (tendency, counts)
+        with counts of adds (incl. subtracts), multiplies, divides and square
+        roots on state values."""
+        x = self._in(st)
+        t = self.zeros()
+        ops = (ctypes.c_ulonglong * 4)()
+        lib().orc_tendency_opcount(self._h, *[_dp(a) for a in x], *[_dp(t[f]) for f in FIELDS], terms, ops)
+        return t, dict(zip(("add", "mul", "div", "sqrt"), [int(v) for v in ops]))
 
     def step(self, st, dt, nsteps=1, terms=TERM_ALL):
         x = [a.copy() for a in self._in(st)]

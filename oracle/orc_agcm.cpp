@@ -71,6 +71,36 @@ inline Dual sqrt(Dual a) {
 }
 inline double sqrt(double a) { return std::sqrt(a); }
 
+// ---- operation counter: a double that tallies the arithmetic it takes part
+// in (one count per add/subtract, multiply, divide, square root).  Used only
+// to state the scheme's operations per grid point; results are bit-identical
+// to the plain double instantiation.
+struct OpTally {
+  unsigned long long add = 0, mul = 0, div = 0, sqrt = 0;
+};
+static OpTally g_tally;
+struct Cnt {
+  double v;
+  Cnt() : v(0) {}
+  Cnt(double x) : v(x) {}
+};
+inline Cnt operator+(Cnt a, Cnt b) { ++g_tally.add; return Cnt(a.v + b.v); }
+inline Cnt operator-(Cnt a, Cnt b) { ++g_tally.add; return Cnt(a.v - b.v); }
+inline Cnt operator-(Cnt a) { return Cnt(-a.v); }
+inline Cnt operator*(Cnt a, Cnt b) { ++g_tally.mul; return Cnt(a.v * b.v); }
+inline Cnt operator/(Cnt a, Cnt b) { ++g_tally.div; return Cnt(a.v / b.v); }
+inline Cnt operator+(Cnt a, double b) { return a + Cnt(b); }
+inline Cnt operator+(double a, Cnt b) { return Cnt(a) + b; }
+inline Cnt operator-(Cnt a, double b) { return a - Cnt(b); }
+inline Cnt operator-(double a, Cnt b) { return Cnt(a) - b; }
+inline Cnt operator*(Cnt a, double b) { return a * Cnt(b); }
+inline Cnt operator*(double a, Cnt b) { return Cnt(a) * b; }
+inline Cnt operator/(Cnt a, double b) { return a / Cnt(b); }
+inline Cnt operator/(double a, Cnt b) { return Cnt(a) / b; }
+inline Cnt& operator+=(Cnt& a, Cnt b) { a = a + b; return a; }
+inline Cnt& operator-=(Cnt& a, Cnt b) { a = a - b; return a; }
+inline Cnt sqrt(Cnt a) { ++g_tally.sqrt; return Cnt(std::sqrt(a.v)); }
+
 // ---- Eq. 7 ------------------------------------------------------------
 // ratio of the 45-degree zonal spacing to the spacing at colatitude theta;
 // cos(90deg - theta) = sin(theta) and res = the zonal grid step.
@@ -506,6 +536,28 @@ void orc_get_leap(void* h, int32_t* Mu, int32_t* Mv) {
 void orc_tendency(void* h, const double* U, const double* V, const double* Ph, const double* pi,
                   double* tU, double* tV, double* tPh, double* tpi, unsigned terms) {
   tendency<double>(*static_cast<Grid*>(h), U, V, Ph, pi, tU, tV, tPh, tpi, terms);
+}
+
+// The tendency through the counting type: writes the tendency (identical to
+// orc_tendency) and ops[4] = adds, multiplies, divides, square roots of one
+// evaluation on state values (geometry-only products are table work, not
+// counted).
+void orc_tendency_opcount(void* h, const double* U, const double* V, const double* Ph, const double* pi,
+                          double* tU, double* tV, double* tPh, double* tpi, unsigned terms,
+                          unsigned long long* ops) {
+  const Grid& g = *static_cast<Grid*>(h);
+  const size_t n3 = (size_t)g.K * g.J * g.I, nv = (size_t)g.K * (g.J - 1) * g.I, n2 = (size_t)g.J * g.I;
+  std::vector<Cnt> u(U, U + n3), v(V, V + nv), p(Ph, Ph + n3), q(pi, pi + n2);
+  std::vector<Cnt> tu(n3), tv(std::max<size_t>(nv, 1)), tp(n3), tq(n2);
+  g_tally = OpTally();
+  tendency<Cnt>(g, u.data(), v.data(), p.data(), q.data(), tu.data(), tv.data(), tp.data(), tq.data(), terms);
+  ops[0] = g_tally.add;
+  ops[1] = g_tally.mul;
+  ops[2] = g_tally.div;
+  ops[3] = g_tally.sqrt;
+  for (size_t n = 0; n < n3; ++n) { tU[n] = tu[n].v; tPh[n] = tp[n].v; }
+  for (size_t n = 0; n < nv; ++n) tV[n] = tv[n].v;
+  for (size_t n = 0; n < n2; ++n) tpi[n] = tq[n].v;
 }
 
 void orc_step(void* h, double* U, double* V, double* Ph, double* pi, double dt, int nsteps,

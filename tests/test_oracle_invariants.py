@@ -359,3 +359,19 @@ def test_rejects_bad_tables():
         oracle.Oracle(16, 8, 2, leap_u=np.full(8, 9))  # 2M >= nlon
     with pytest.raises(ValueError):
         oracle.Oracle(16, 8, 2, sigma_half=[0.0, 0.6, 0.5])  # non-monotone sigma
+
+
+def test_operation_count_is_faithful_and_stride_free():
+    """The counting type changes no result, and its tally is the same per grid
+    point whatever the leap strides (doubling nlon changes every stride)."""
+    counts = []
+    for I in (32, 64):
+        J, K = 16, 4
+        st = inputs.random_state(I, J, K, seed=5)
+        o = oracle.Oracle(I, J, K, phis=st["phis"])
+        t, ops = o.tendency_opcount(st)
+        t0 = o.tendency(st)
+        assert all(np.array_equal(t[f], t0[f]) for f in t0)
+        assert min(ops.values()) > 0
+        counts.append(ops)
+    assert all(counts[1][k] == 2 * counts[0][k] for k in counts[0])

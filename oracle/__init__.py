@@ -63,6 +63,11 @@ def lib():
         _lib.orc_filter_band.restype = ctypes.c_int
         _lib.orc_filter_band.argtypes = [ctypes.c_double]
         _lib.orc_filter.argtypes = [vp] + [d] * 4 + [ctypes.c_double]
+        _lib.orc_set_thermo.restype = ctypes.c_int
+        _lib.orc_set_thermo.argtypes = [vp, d]
+        _lib.orc_std_temp.restype = ctypes.c_double
+        _lib.orc_std_temp.argtypes = [d, ctypes.c_double]
+        _lib.orc_std_surface.argtypes = [d, ctypes.c_double, d]
         _lib.orc_tendency_opcount.argtypes = [vp] + [d] * 8 + [ctypes.c_uint, ctypes.POINTER(ctypes.c_ulonglong)]
     return _lib
 
@@ -99,11 +104,40 @@ def leap_table(nlon: int, nlat: int):
 
 FIELDS = ("U", "V", "Phi", "pi")
 
+# Standard stratification and Eq. 1's switches (readings T1..T4); the default
+# is the isothermal 250 K atmosphere with every switch off.
+THERMO_DEFAULT = dict(profile=0, T0=250.0, Ts0=288.15, lapse=6.5e-3, Ttrop=216.65, delta=0.0, delta_c=0.0,
+                      delta_p=0.0)
+_THERMO_KEYS = ("profile", "T0", "Ts0", "lapse", "Ttrop", "delta", "delta_c", "delta_p")
+
+
+def _thermo_vec(thermo):
+    t = dict(THERMO_DEFAULT)
+    t.update(thermo or {})
+    unknown = set(t) - set(_THERMO_KEYS)
+    if unknown:
+        raise ValueError(f"unknown thermo keys {sorted(unknown)}")
+    return np.array([float(t[k]) for k in _THERMO_KEYS])
+
+
+def std_temp(p_over_p0, **thermo):
+    """T~ at p / p0 of the standard stratification (reading T1)."""
+    v = _thermo_vec(thermo)
+    return lib().orc_std_temp(_dp(v), float(p_over_p0))
+
+
+def std_surface(phis, **thermo):
+    """(pi~, T~_s): standard surface pressure / p0 and temperature under phis (T3)."""
+    v = _thermo_vec(thermo)
+    out = np.zeros(2)
+    lib().orc_std_surface(_dp(v), float(phis), _dp(out))
+    return float(out[0]), float(out[1])
+
 
 class Oracle:
     """One grid of the oracle.  ``state`` arguments are dicts with keys U, V, Phi, pi."""
 
-    def __init__(self, nlon, nlat, nlev, sigma_half=None, leap_u=None, leap_v=None, phis=None):
+    def __init__(self, nlon, nlat, nlev, sigma_half=None, leap_u=None, leap_v=None, phis=None, thermo=None):
         self.I, self.J, self.K = int(nlon), int(nlat), int(nlev)
         keep = []
 
@@ -129,6 +163,10 @@ class Oracle:
         )
         if not self._h:
             raise ValueError("oracle rejected the grid arguments")
+        if thermo is not None:
+            v = _thermo_vec(thermo)
+            if L.orc_set_thermo(self._h, _dp(v)) != 0:
+                raise ValueError("oracle rejected the thermo arguments")
         self.leap_u = np.zeros(self.J, np.int32)
         self.leap_v = np.zeros(max(self.J - 1, 1), np.int32)
         L.orc_get_leap(self._h, _ip(self.leap_u), _ip(self.leap_v))

@@ -38,8 +38,9 @@ const double kA = 6.371e6;        // Earth radius [m]
 const double kOmega = 7.292e-5;   // rotation rate [1/s]
 const double kR = 287.04;         // gas constant of dry air
 const double kCp = 1004.64;       // heat capacity at constant pressure
-const double kT0 = 250.0;         // isothermal standard stratification [K]
+const double kT0 = 250.0;         // default isothermal standard stratification [K] (reading R2)
 const double kPi = 3.14159265358979323846;
+const double kG = 9.80665;        // gravity, for the standard atmosphere's lapse rate [m/s^2]
 
 // ---- forward-mode dual number: value + one directional derivative --------
 struct Dual {
@@ -121,6 +122,49 @@ int leap_stride(double theta, double dlam) {
   return n;
 }
 
+// ---- standard stratification and the Eq. 1 coefficient of Omega~ ----------
+// Eq. 1 subtracts a standard stratification T~(p) and scales the Omega~ term
+// of the Phi equation by (1 - delta_p)[b(1 + delta_c) + delta kappa Phi / P];
+// the paper defines neither T~ nor the deltas (readings T1..T4).
+struct Thermo {
+  int profile = 0;     // 0: isothermal T0; 1: lapse rate to a tropopause, isothermal above (T1)
+  double T0 = kT0;     // isothermal temperature [K]
+  double Ts0 = 288.15, lapse = 6.5e-3, Ttrop = 216.65;  // profile 1: T at p0, -dT/dz, tropopause T
+  double delta = 0.0, delta_c = 0.0, delta_p = 0.0;    // Eq. 1's switches (T4)
+};
+
+// T~ at p / p0 (T1): profile 1 is T = Ts0 (p/p0)^(R lapse / g), not below Ttrop.
+double std_temp(const Thermo& t, double p) {
+  if (t.profile == 0) return t.T0;
+  if (t.lapse == 0.0) return t.Ts0;
+  return std::fmax(t.Ts0 * std::pow(p, kR * t.lapse / kG), t.Ttrop);
+}
+
+// Standard surface pressure / p0 and temperature under surface geopotential
+// phis: the hydrostatic column of T~ from p0 at phi = 0 (T3).
+void std_surface(const Thermo& t, double phis, double* pit, double* Ts) {
+  if (t.profile == 0) {
+    *pit = std::exp(-phis / (kR * t.T0));
+    *Ts = t.T0;
+    return;
+  }
+  if (t.lapse == 0.0) {
+    *pit = std::exp(-phis / (kR * t.Ts0));
+    *Ts = t.Ts0;
+    return;
+  }
+  const double z = phis / kG, ex = kG / (kR * t.lapse);
+  const double T = t.Ts0 - t.lapse * z;
+  if (T >= t.Ttrop) {
+    *pit = std::pow(T / t.Ts0, ex);
+    *Ts = T;
+  } else {
+    const double ztr = (t.Ts0 - t.Ttrop) / t.lapse;
+    *pit = std::pow(t.Ttrop / t.Ts0, ex) * std::exp(-kG * (z - ztr) / (kR * t.Ttrop));
+    *Ts = t.Ttrop;
+  }
+}
+
 struct Grid {
   int I = 0, J = 0, K = 0;
   double dlam = 0, dth = 0;
@@ -132,8 +176,31 @@ struct Grid {
   // sigma: half levels sh[0..K] with sh[0] = 0 (model top) and sh[K] = 1
   std::vector<double> sh, ds, H;  // H is K x K, row-major
   std::vector<double> pit;        // standard surface pressure / p0, J x I
-  double b = 0;                   // IAP constant b = sqrt(kappa R T0)
+  std::vector<double> rts;        // R T~_s of each column, J x I (T3)
+  std::vector<double> phis;       // surface geopotential, J x I
+  std::vector<double> beta;       // (1 - delta_p)(1 + delta_c) b_k, b_k = sqrt(kappa R T~(sigma_k)) (T2)
+  double beta2 = 0;               // (1 - delta_p) delta kappa: the Phi-dependent part of the coefficient
+  Thermo th;
 };
+
+// The thermodynamic tables of a grid from its Thermo (T1..T4).
+void apply_thermo(Grid& g) {
+  const Thermo& t = g.th;
+  const double kap = kR / kCp;
+  g.beta.resize(g.K);
+  for (int k = 0; k < g.K; ++k) {
+    const double sig = 0.5 * (g.sh[k] + g.sh[k + 1]);
+    g.beta[k] = (1.0 - t.delta_p) * (1.0 + t.delta_c) * std::sqrt(kap * kR * std_temp(t, sig));
+  }
+  g.beta2 = (1.0 - t.delta_p) * t.delta * kap;
+  g.pit.resize((size_t)g.J * g.I);
+  g.rts.resize(g.pit.size());
+  for (size_t n = 0; n < g.pit.size(); ++n) {
+    double Ts = 0;
+    std_surface(t, g.phis[n], &g.pit[n], &Ts);
+    g.rts[n] = kR * Ts;
+  }
+}
 
 // ---- storage helpers ---------------------------------------------------
 struct Ix {
@@ -162,7 +229,7 @@ void tendency(const Grid& g, const T* U, const T* V, const T* Ph, const T* pi, T
               T* tV, T* tPh, T* tpi, unsigned terms) {
   const int I = g.I, J = g.J, K = g.K, JV = J - 1;
   const Ix x{I, J, K};
-  const double a = kA, dlam = g.dlam, dth = g.dth, b = g.b;
+  const double a = kA, dlam = g.dlam, dth = g.dth;
 
   // a2: mass m = p_es/p0 = pi~ + pi, P = sqrt(m); P at U and V points from
   //     the stride-1 mean of m (reading: P^2 at a face is the mean mass).
@@ -220,16 +287,24 @@ void tendency(const Grid& g, const T* U, const T* V, const T* Ph, const T* pi, T
       }
     }
 
-  // a5: psi = phi' + R T0 pi / pi~, with phi'_k = sum_k' H[k][k'] (b/P) Phi_k'
-  //     (hydrostatic integral from the surface, reading R7).
+  // Eq. 1's coefficient of Omega~ at (k, j, i): c = beta_k + beta2 Phi / P
+  //     (reading T4; beta2 = 0 unless the delta kappa Phi / P term is on).
+  auto coef = [&](int k, int j, int i) -> T {
+    if (g.beta2 == 0.0) return T(g.beta[k]);
+    return g.beta[k] + g.beta2 * Ph[x.s3(k, j, i)] / P[x.s2(j, i)];
+  };
+
+  // a5: psi = phi' + R T~_s pi / pi~, with phi'_k = sum_k' H[k][k'] (c/P) Phi_k'
+  //     (hydrostatic integral from the surface, reading R7; isothermal
+  //     T~ = T0 gives c = b).
   std::vector<T> psi(n3);
   for (int j = 0; j < J; ++j)
     for (int i = 0; i < I; ++i) {
-      const T bP = b / P[x.s2(j, i)];
-      const T ps = kR * kT0 * pi[x.s2(j, i)] / g.pit[x.s2(j, i)];
+      const T ps = g.rts[x.s2(j, i)] * pi[x.s2(j, i)] / g.pit[x.s2(j, i)];
       for (int k = 0; k < K; ++k) {
         T phi = 0.0;
-        for (int kk = 0; kk < K; ++kk) phi += g.H[(size_t)k * K + kk] * (bP * Ph[x.s3(kk, j, i)]);
+        for (int kk = 0; kk < K; ++kk)
+          phi += g.H[(size_t)k * K + kk] * ((coef(kk, j, i) / P[x.s2(j, i)]) * Ph[x.s3(kk, j, i)]);
         T val = 0.0;
         if (terms & TERM_PGF_PHI) val += phi;
         if (terms & TERM_PGF_PI) val += ps;
@@ -260,16 +335,15 @@ void tendency(const Grid& g, const T* U, const T* V, const T* Ph, const T* pi, T
           tV[x.v3(k, j, i)] -= Pv[x.s2(j, i)] * grad;
         }
   }
-  // a7: Omega~ conversion, the exact H-transpose of a5:
-  //     dPhi_k/dt += -(b/P) (1/dsigma_k) sum_k' H[k'][k] dsigma_k' D_k'.
+  // a7: Omega~ conversion, the exact H-transpose of a5 with the same c:
+  //     dPhi_k/dt += -(c/P) (1/dsigma_k) sum_k' H[k'][k] dsigma_k' D_k'.
   if (terms & TERM_PGF_PHI) {
     for (int j = 0; j < J; ++j)
       for (int i = 0; i < I; ++i) {
-        const T bP = b / P[x.s2(j, i)];
         for (int k = 0; k < K; ++k) {
           T acc = 0.0;
           for (int kk = 0; kk < K; ++kk) acc += g.H[(size_t)kk * K + k] * (g.ds[kk] * D[x.s3(kk, j, i)]);
-          tPh[x.s3(k, j, i)] -= bP * acc / g.ds[k];
+          tPh[x.s3(k, j, i)] -= (coef(k, j, i) / P[x.s2(j, i)]) * acc / g.ds[k];
         }
       }
   }
@@ -482,7 +556,6 @@ void* orc_create(int I, int J, int K, const double* sigma_half, const int32_t* M
   g->I = I; g->J = J; g->K = K;
   g->dlam = 2.0 * kPi / I;
   g->dth = kPi / J;
-  g->b = std::sqrt((kR / kCp) * kR * kT0);
   g->s.resize(J); g->c.resize(J); g->cot.resize(J); g->A.resize(J); g->Mu.resize(J);
   g->sv.resize(J - 1); g->Av.resize(J - 1); g->Mv.resize(J - 1);
   for (int j = 0; j < J; ++j) {
@@ -519,13 +592,43 @@ void* orc_create(int I, int J, int K, const double* sigma_half, const int32_t* M
     g->H[(size_t)k * K + k] = std::log(g->sh[k + 1] / sig);
     for (int kk = k + 1; kk < K; ++kk) g->H[(size_t)k * K + kk] = std::log(g->sh[kk + 1] / g->sh[kk]);
   }
-  // reading R2: pi~ = exp(-phi_s / (R T0)), the isothermal standard surface pressure
-  g->pit.resize((size_t)J * I);
-  for (size_t n = 0; n < (size_t)J * I; ++n) g->pit[n] = std::exp(-(phis ? phis[n] : 0.0) / (kR * kT0));
+  // reading R2: by default pi~ = exp(-phi_s / (R T0)), the isothermal standard
+  // surface pressure, and b = sqrt(kappa R T0) on every level
+  g->phis.assign((size_t)J * I, 0.0);
+  if (phis) g->phis.assign(phis, phis + (size_t)J * I);
+  apply_thermo(*g);
   return g;
 }
 
 void orc_destroy(void* h) { delete static_cast<Grid*>(h); }
+
+// p = {profile, T0, Ts0, lapse, Ttrop, delta, delta_c, delta_p}; returns 0, or
+// -1 for values outside their range (the grid is then unchanged).
+int orc_set_thermo(void* h, const double* p) {
+  Thermo t;
+  t.profile = (int)p[0];
+  t.T0 = p[1]; t.Ts0 = p[2]; t.lapse = p[3]; t.Ttrop = p[4];
+  t.delta = p[5]; t.delta_c = p[6]; t.delta_p = p[7];
+  if ((t.profile != 0 && t.profile != 1) || !(t.T0 > 0) || !(t.Ts0 > 0) || !(t.lapse >= 0) || !(t.Ttrop > 0) ||
+      t.Ttrop > t.Ts0 || !(t.delta_c > -1) || !(t.delta_p >= 0 && t.delta_p <= 1) || !std::isfinite(t.delta))
+    return -1;
+  Grid& g = *static_cast<Grid*>(h);
+  g.th = t;
+  apply_thermo(g);
+  return 0;
+}
+
+double orc_std_temp(const double* p, double p_over_p0) {
+  Thermo t;
+  t.profile = (int)p[0]; t.T0 = p[1]; t.Ts0 = p[2]; t.lapse = p[3]; t.Ttrop = p[4];
+  return std_temp(t, p_over_p0);
+}
+
+void orc_std_surface(const double* p, double phis, double* out) {
+  Thermo t;
+  t.profile = (int)p[0]; t.T0 = p[1]; t.Ts0 = p[2]; t.lapse = p[3]; t.Ttrop = p[4];
+  std_surface(t, phis, out, out + 1);
+}
 
 void orc_get_leap(void* h, int32_t* Mu, int32_t* Mv) {
   const Grid* g = static_cast<Grid*>(h);
@@ -637,7 +740,7 @@ void orc_diagnostics(void* h, const double* U, const double* V, const double* Ph
     for (int i = 0; i < I; ++i) {
       const double p = pi[x.s2(j, i)];
       mass += g.A[j] * (g.pit[x.s2(j, i)] + p);
-      eps += 0.5 * g.A[j] * (kR * kT0 / g.pit[x.s2(j, i)]) * p * p;
+      eps += 0.5 * g.A[j] * (g.rts[x.s2(j, i)] / g.pit[x.s2(j, i)]) * p * p;
       finite = finite && std::isfinite(p);
     }
   for (int k = 0; k < K; ++k)

@@ -192,7 +192,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
-    ap.add_argument("--only", choices=["adjoint", "ensemble", "fp64", "fp32_720", "split", "filter"],
+    ap.add_argument("--only", choices=["adjoint", "ensemble", "fp64", "fp32_720", "split", "filter", "thermo"],
                     help="measure one form alone and print its JSON (for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -337,6 +337,8 @@ def run_only(form):
         out = measure_split(agcm, inputs, torch, steps=3)
     elif form == "filter":
         out = measure_filter(agcm, inputs, torch, reps=3)
+    elif form == "thermo":
+        out = measure_thermo(agcm, inputs, torch, steps=3)
     else:  # fp64: the plain FP64 step at the bench size; fp32_720: FP32 at 720x360x30
         I, J, K = WORKLOAD if form == "fp64" else (720, 360, 30)
         st = inputs.baroclinic_jet(I, J, K, seed=6, noise=1e-2, terrain_seed=2)
@@ -394,6 +396,10 @@ def measure_forms(agcm, inputs, torch, steps=5):
     except Exception as e:
         out["split_1440x720x30"] = {"error": repr(e)}
     try:
+        out["thermo_1440x720x30"] = measure_thermo(agcm, inputs, torch)
+    except Exception as e:
+        out["thermo_1440x720x30"] = {"error": repr(e)}
+    try:
         out["filter_1440x720x30"] = measure_filter(agcm, inputs, torch)
     except Exception as e:
         out["filter_1440x720x30"] = {"error": repr(e)}
@@ -426,6 +432,27 @@ def measure_split(agcm, inputs, torch, steps=5):
            "hbm_frac_step": pts / (ms / 1e3) * words * 4 / (peaks()[0] * 1e9),
            "sypd_equiv": pts / (ms / 1e3) / pts * dt / 365.0,
            "finite": bool(s.diagnostics()["finite"])}
+    s.close()
+    return res
+
+
+THERMO_FULL = dict(profile=1, Ts0=288.15, lapse=6.5e-3, Ttrop=216.65, delta=1.0, delta_c=0.0, delta_p=0.0)
+
+
+def measure_thermo(agcm, inputs, torch, steps=5):
+    """The step at 1440x720x30 FP32 with Eq. 1's thermodynamics on: a
+    lapse-rate standard atmosphere (per-level b) and the nonlinear
+    delta kappa Phi/P term."""
+    I, J, K = WORKLOAD
+    st = inputs.baroclinic_jet(I, J, K, seed=6, noise=1e-2, terrain_seed=2)
+    g = agcm.Grid(I, J, K, phis=st["phis"], thermo=THERMO_FULL)
+    dt = g.dt(100.0)
+    s = agcm.State(g, agcm.AGCM_FP32)
+    s.load(st)
+    s.step(2, dt)
+    ms = _time(torch, lambda: s.step(steps, dt), 1) / steps
+    res = {"value": I * J * K / (ms / 1e3), "unit": "gp-steps/s", "ms_per_step": ms, "dt_s": dt,
+           "thermo": THERMO_FULL, "finite": bool(s.diagnostics()["finite"])}
     s.close()
     return res
 

@@ -86,13 +86,44 @@ int agcm_grid_create(int nlon, int nlat, int nlev, const double* sigma_half, con
                      const int32_t* leap_v, const double* phis, agcm_grid_t** out);
 int agcm_grid_destroy(agcm_grid_t* grid);
 
+/*
+ * agcm_grid_set_thermo — the standard stratification and the switches of
+ * Eq. 1's Phi equation, (1 - delta_p)[b(1 + delta_c) + delta kappa Phi/P]
+ * times the Omega~ term.  The paper defines neither T~(p) nor the deltas;
+ * this library reads them as follows (host only, no device work):
+ *   profile 0: isothermal T~ = T0 (the default: T0 = 250 K, every delta 0);
+ *   profile 1: T~(p) = Ts0 (p/p0)^(R lapse/g), not below Ttrop (a lapse-rate
+ *              troposphere under an isothermal stratosphere), g = 9.80665.
+ *   b_k = sqrt(kappa R T~(sigma_k)) at each layer's mid sigma; the standard
+ *   surface pressure pi~ and temperature T~_s under phis follow from the
+ *   hydrostatic column of T~ starting at p0 where phi = 0, and the surface
+ *   part of the pressure gradient is R T~_s pi / pi~.  The coefficient c
+ *   above multiplies Phi/P in the hydrostatic integral as well as the Omega~
+ *   conversion, so the spatial operator stays energy neutral.
+ *   Ranges: profile 0 or 1; T0, Ts0, Ttrop > 0; Ttrop <= Ts0; lapse >= 0;
+ *   delta finite; delta_c > -1; 0 <= delta_p <= 1.  NULL restores the
+ *   default.  Must be called before the first state on the grid is created
+ *   (the device tables are built then): AGCM_EINVAL afterwards.
+ *   With delta != 0 (the nonlinear delta kappa Phi/P term) the adjoint step
+ *   and ensembles return AGCM_EINVAL.
+ */
+typedef struct agcm_thermo {
+  int profile;
+  double T0, Ts0, lapse, Ttrop;
+  double delta, delta_c, delta_p;
+} agcm_thermo_t;
+int agcm_grid_set_thermo(agcm_grid_t* grid, const agcm_thermo_t* thermo);
+
 /* Copy the stride tables out (leap_u: nlat values, leap_v: nlat-1 values). */
 int agcm_grid_leap(const agcm_grid_t* grid, int32_t* leap_u, int32_t* leap_v);
 
 /*
- * Time step from the gravity-wave bound (reading R10 of the design notes):
+ * Time step from the gravity-wave bound (the paper gives no dt; Sec.
+ * "Filtering" only states the CFL condition dt <= dx / U):
  * dt = 1.6 / ((c_max + umax) * sqrt((2/(a cos45 dlam))^2 + (2/(a dth))^2)),
- * c_max^2 the largest eigenvalue of the linear column operator.  Host only.
+ * c_max^2 the largest eigenvalue of the linear column operator with the
+ * level coefficients (1 - delta_p)(1 + delta_c) b_k and the largest R T~_s of
+ * the grid.  Host only.
  */
 int agcm_grid_dt(const agcm_grid_t* grid, double umax, double* dt);
 
@@ -240,7 +271,7 @@ int agcm_ensemble_profile(agcm_ensemble_t* ens, int enable, double* ms_total, in
  *   U, V, Phi, pi: caller-owned device input (layout above, element type of
  *           `precision`); tU, tV, tPhi, tpi: caller-owned device output.
  * The call allocates nothing: its scratch (the grid's device tables and the
- * FP64 vertical means, about 11 MB) is one fixed array that every GPU holds
+ * FP64 vertical means, about 13 MB) is one fixed array that every GPU holds
  * from library load until process exit.  Every call overwrites that array, so
  * calls whose kernels overlap on a GPU (other streams, other threads) race;
  * serialise them.  The first call on a device looks up the array's device

@@ -15,8 +15,8 @@
 //   Table "Communication aggregation of leap-format difference variables":
 //           staggered pairs span an odd stride M, centred pairs span +-M
 //   Alg. 1 / Alg. 2   vertical sum and prefix sum that give the sigma velocity
-// Where the paper is silent the code follows the readings listed in the
-// repository's design notes (R1..R11); each is named at the place it is used.
+// Where the paper is silent the code takes a reading (R1..R11, F1..F4,
+// T1..T4); each is stated at the place it is used.
 //
 // Parity status: pinned by the tests under tests/ (energy and mass
 // conservation, piecewise skewness, reduction to Eq. 5, closed forms of the

@@ -62,12 +62,25 @@ _alloc_cbs = None
 # symbol -> (restype, argtypes)
 _vp, _i, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
 _pi32, _pd = ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)
+class Thermo(ctypes.Structure):
+    """agcm_thermo_t: standard stratification and Eq. 1's switches."""
+
+    _fields_ = [("profile", ctypes.c_int), ("T0", ctypes.c_double), ("Ts0", ctypes.c_double),
+                ("lapse", ctypes.c_double), ("Ttrop", ctypes.c_double), ("delta", ctypes.c_double),
+                ("delta_c", ctypes.c_double), ("delta_p", ctypes.c_double)]
+
+
+THERMO_DEFAULT = dict(profile=0, T0=250.0, Ts0=288.15, lapse=6.5e-3, Ttrop=216.65, delta=0.0, delta_c=0.0,
+                      delta_p=0.0)
+
+
 SIGNATURES = {
     "agcm_last_error": (ctypes.c_char_p, []),
     "agcm_version": (_i, []),
     "agcm_set_allocator": (_i, [_vp, _vp, _vp]),
     "agcm_grid_create": (_i, [_i, _i, _i, _pd, _pi32, _pi32, _pd, ctypes.POINTER(_vp)]),
     "agcm_grid_destroy": (_i, [_vp]),
+    "agcm_grid_set_thermo": (_i, [_vp, ctypes.POINTER(Thermo)]),
     "agcm_grid_leap": (_i, [_vp, _pi32, _pi32]),
     "agcm_grid_dt": (_i, [_vp, _d, _pd]),
     "agcm_state_create": (_i, [_vp, _i, _i, ctypes.POINTER(_vp)]),
@@ -158,7 +171,7 @@ def _np_opt(a, dtype, n):
 class Grid:
     """agcm_grid_create / agcm_grid_leap / agcm_grid_dt."""
 
-    def __init__(self, nlon, nlat, nlev, sigma_half=None, leap_u=None, leap_v=None, phis=None):
+    def __init__(self, nlon, nlat, nlev, sigma_half=None, leap_u=None, leap_v=None, phis=None, thermo=None):
         self.nlon, self.nlat, self.nlev = int(nlon), int(nlat), int(nlev)
         _, psh = _np_opt(sigma_half, np.float64, self.nlev + 1)
         _, plu = _np_opt(leap_u, np.int32, self.nlat)
@@ -168,6 +181,18 @@ class Grid:
         h = _vp()
         check(lib().agcm_grid_create(self.nlon, self.nlat, self.nlev, psh, plu, plv, pph, ctypes.byref(h)))
         self._h = h
+        if thermo is not None:
+            self.set_thermo(**thermo)
+
+    def set_thermo(self, **kw):
+        """agcm_grid_set_thermo: keys of THERMO_DEFAULT; before the first state."""
+        t = dict(THERMO_DEFAULT)
+        unknown = set(kw) - set(t)
+        if unknown:
+            raise ValueError(f"unknown thermo keys {sorted(unknown)}")
+        t.update(kw)
+        v = Thermo(int(t["profile"]), *(float(t[k]) for k in list(THERMO_DEFAULT)[1:]))
+        check(lib().agcm_grid_set_thermo(self._h, ctypes.byref(v)))
 
     @property
     def handle(self):

@@ -313,8 +313,9 @@ __global__ void __launch_bounds__(256) k_adj_update(Geom<T> g, const T* __restri
 //   D_k  = (Fl[fE] - Fl[fW]) rdx + (sv_j Ft_j - sv_{j-1} Ft_{j-1}) rdy
 //   C    = sum_k ds_k D_k;  dpi/dt = -C
 //   W_h  = sh_h C - sum_{k<h} ds_k D_k               (h = 1..K-1)
-//   B_k  = b rP Phi_k;  psi_k = sum_k' H[k][k'] B_k' + R T0 pi / pi~
-//   X_k  = -(b rP) (1/ds_k) sum_k' H[k'][k] ds_k' D_k'
+//   B_k  = rP Phi_k;  psi_k = sum_k' H[k][k'] B_k' + R T~_s pi / pi~
+//   X_k  = -rP (1/ds_k) sum_k' H[k'][k] ds_k' D_k'
+//   (H carries the level coefficient beta of its source level)
 template <class T>
 __global__ void __launch_bounds__(128) k_adj_column(Geom<T> g, const T* __restrict__ Phi, ColState<T> cs,
                                                     const T* __restrict__ X, const T* __restrict__ yPhi,
@@ -325,7 +326,7 @@ __global__ void __launch_bounds__(128) k_adj_column(Geom<T> g, const T* __restri
   const int j = n / I, i = n - j * I;
   const size_t plane = (size_t)J * I;
   const T rPc = cs.rP[n];
-  const T bP = g.b * rPc;
+  const T bP = rPc;  // the level coefficient sits in the H tables
   // C-bar = -ypi + sum_h sh_h Wbar_h
   double Cb = -(double)ypi[n];
   for (int h = 1; h < K; ++h) Cb += g.shd[h] * (double)a.aW[(size_t)h * plane + n];
@@ -338,7 +339,7 @@ __global__ void __launch_bounds__(128) k_adj_column(Geom<T> g, const T* __restri
     psum += pb;
     const T ph = Phi[(size_t)k * plane + n];
     a.aPhi[(size_t)k * plane + n] = Bb * bP;
-    arp += Bb * g.b * ph;
+    arp += Bb * ph;
   }
   // X: dX_k/drP = X_k / rP
   for (int k = 0; k < K; ++k) arp += yPhi[(size_t)k * plane + n] * X[(size_t)k * plane + n] / rPc;

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -74,7 +75,8 @@ constexpr double kA = 6.371e6;
 constexpr double kOmega = 7.292e-5;
 constexpr double kR = 287.04;
 constexpr double kCp = 1004.64;
-constexpr double kT0 = 250.0;
+constexpr double kT0 = 250.0;     // default isothermal standard stratification [K]
+constexpr double kG = 9.80665;    // gravity, for the lapse-rate standard atmosphere
 constexpr double kPi = 3.14159265358979323846;
 
 // Eq. 7 with cos(90deg - theta) = sin(theta) and res = dlam, rounded up to an
@@ -98,8 +100,14 @@ struct DevGeomBlob {
 
 struct agcm_grid {
   int I = 0, J = 0, K = 0;
-  double dlam = 0, dth = 0, b = 0;
+  double dlam = 0, dth = 0;
   std::vector<double> s, c, cot, A, sv, Av, sh, ds, Hkk, hk, pit;
+  // thermodynamics (agcm_grid_set_thermo): surface geopotential, the level
+  // coefficients beta_k = (1 - delta_p)(1 + delta_c) b_k, beta2 = (1 - delta_p)
+  // delta kappa, and R T~_s of each column
+  std::vector<double> phis, beta, rts;
+  double beta2 = 0;
+  agcm_thermo_t th{0, kT0, 288.15, 6.5e-3, 216.65, 0.0, 0.0, 0.0};
   std::vector<int> Mu, Mv;
   // device copies of the tables, per precision (0 = FP64, 1 = FP32)
   DevGeomBlob dev[2];
@@ -245,11 +253,17 @@ int upload_geom(agcm_grid* g, int p) {
     cn[j] = 0.25 * g->A[j] / g->Av[j];
     cs[j] = 0.25 * g->A[j + 1] / g->Av[j];
   }
-  std::vector<double> r2ds(K), hk_rds(K), oms(K);
+  // the hydrostatic weights carry the level coefficient beta_k (Eq. 1's
+  // (1 - delta_p) b (1 + delta_c)), so no kernel multiplies by b; rho_k =
+  // beta2 / beta_k scales the delta kappa Phi/P part relative to it
+  std::vector<double> r2ds(K), Hkkb(K), hkb(K), hk_rds(K), oms(K), rho(K);
   for (int k = 0; k < K; ++k) {
     r2ds[k] = 0.5 / g->ds[k];
-    hk_rds[k] = g->hk[k] / g->ds[k];
+    Hkkb[k] = g->beta[k] * g->Hkk[k];
+    hkb[k] = g->beta[k] * g->hk[k];
+    hk_rds[k] = g->beta[k] * g->hk[k] / g->ds[k];
     oms[k] = 1.0 - g->sh[k];
+    rho[k] = g->beta[k] != 0.0 ? g->beta2 / g->beta[k] : 0.0;
   }
   // low-latitude filter bands (Table "Conventional Filtering scheme")
   auto band_of = [](double colat) {
@@ -269,7 +283,7 @@ int upload_geom(agcm_grid* g, int p) {
   filtU.push_back(0);
   filtV.push_back(0);
   std::vector<double> rt0pit((size_t)J * I);
-  for (size_t n = 0; n < rt0pit.size(); ++n) rt0pit[n] = kR * kT0 / g->pit[n];
+  for (size_t n = 0; n < rt0pit.size(); ++n) rt0pit[n] = g->rts[n] / g->pit[n];
 
   size_t o_Mu = putI(g->Mu), o_rdx = putT(rdx), o_rdy = putT(rdy), o_zf = putT(zf), o_r2A = putT(r2A),
          o_f0 = putT(f0), o_cota = putT(cota);
@@ -281,8 +295,8 @@ int upload_geom(agcm_grid* g, int p) {
          o_r2Av = putT(r2Av.empty() ? std::vector<double>{0} : r2Av),
          o_cn = putT(cn.empty() ? std::vector<double>{0} : cn),
          o_cs = putT(cs.empty() ? std::vector<double>{0} : cs);
-  size_t o_ds = putT(g->ds), o_r2ds = putT(r2ds), o_hk = putT(g->hk), o_Hkk = putT(g->Hkk),
-         o_hkr = putT(hk_rds), o_oms = putT(oms), o_dsd = putD(g->ds), o_shd = putD(g->sh), o_Ad = putD(g->A),
+  size_t o_ds = putT(g->ds), o_r2ds = putT(r2ds), o_hk = putT(hkb), o_Hkk = putT(Hkkb),
+         o_hkr = putT(hk_rds), o_oms = putT(oms), o_rho = putT(rho), o_dsd = putD(g->ds), o_shd = putD(g->sh), o_Ad = putD(g->A),
          o_Avd = putD(g->Av.empty() ? std::vector<double>{0} : g->Av);
   size_t o_rt0 = putT(rt0pit), o_pit = putT(g->pit);
   size_t o_bu = putI(filtU), o_bv = putI(filtV);
@@ -326,7 +340,8 @@ int upload_geom(agcm_grid* g, int p) {
   G.Avd = (const double*)(base + o_Avd);
   G.rt0pit = (const T*)(base + o_rt0);
   G.pit = (const T*)(base + o_pit);
-  G.b = (T)g->b;
+  G.rho = (const T*)(base + o_rho);
+  G.nl = g->beta2 != 0.0 && g->th.delta != 0.0;
   G.rady = (T)(1.0 / (kA * g->dth));
   g->dev[p].blob = d;
   g->dev[p].ready = true;
@@ -405,7 +420,8 @@ int ensure_bar(agcm_state* s, cudaStream_t st) {
 // (outb < 0: not written).
 // Launch of the stage kernel.  AGCM_STAGE_TILE selects the shape: 0 = one
 // warp per 32-column row segment with global loads (default: fastest on GB300
-// at 1440x720x30, see the design notes), 1 = 32 x 4 tiles staged by TMA.
+// at 1440x720x30: 0.67 ms per stage against 0.96 ms for the tiles), 1 = 32 x 4
+// tiles staged by TMA.
 #ifndef AGCM_STAGE_TILE
 #define AGCM_STAGE_TILE 0
 #endif
@@ -413,15 +429,22 @@ template <class T, int MODE, int TERMS = 3>
 int launch_fused(const agcm::Geom<T>& G, const void* const xs[4], const double* ub, const double* vb,
                  const void* const xb[4], void* const out[4], double* ubo, double* vbo, const double* ubb,
                  const double* vbb, double cdt, int* err, cudaStream_t st) {
-  if constexpr (!AGCM_STAGE_TILE || TERMS != 3) {
+  auto rows = [&](auto nl) -> int {  // one warp per 32 columns of a row
     const dim3 block(agcm::kTileX, 1);
     const dim3 grid((unsigned)((G.I + agcm::kTileX - 1) / agcm::kTileX), (unsigned)G.J);
-    agcm::k_fused_stage<T, MODE, 1, TERMS><<<grid, block, 0, st>>>(
+    agcm::k_fused_stage<T, MODE, 1, TERMS, decltype(nl)::value><<<grid, block, 0, st>>>(
         G, (const T*)xs[0], (const T*)xs[1], (const T*)xs[2], (const T*)xs[3], ub, vb, (const T*)xb[0],
         (const T*)xb[1], (const T*)xb[2], (const T*)xb[3], (T*)out[0], (T*)out[1], (T*)out[2], (T*)out[3], ubo, vbo,
         ubb, vbb, (T)cdt, 0, err);
     CUDA_TRY(cudaGetLastError());
     return AGCM_OK;
+  };
+  // the delta kappa Phi/P term touches only the adaptation terms
+  if constexpr ((TERMS & 2) != 0) {
+    if (G.nl) return rows(std::true_type{});
+  }
+  if constexpr (!AGCM_STAGE_TILE || TERMS != 3) {
+    return rows(std::false_type{});
   } else {
   static bool attr_set = false;  // per process; the attribute is per function
   const size_t smem = agcm::tile_smem_bytes<T>();
@@ -540,6 +563,68 @@ int agcm_set_allocator(agcm_alloc_fn alloc, agcm_free_fn free_fn, void* ctx) {
   return AGCM_OK;
 }
 
+// Standard stratification T~ at p/p0: isothermal, or a lapse-rate troposphere
+// T~ = Ts0 (p/p0)^(R lapse/g) above an isothermal stratosphere at Ttrop.
+static double std_temperature(const agcm_thermo_t& t, double p) {
+  if (t.profile == 0) return t.T0;
+  if (t.lapse == 0.0) return t.Ts0;
+  return std::max(t.Ts0 * std::pow(p, kR * t.lapse / kG), t.Ttrop);
+}
+
+// Standard surface pressure / p0 and temperature under phis: hydrostatic
+// balance of T~ from p0 at phi = 0 (closed forms of the two layers).
+static void std_surface(const agcm_thermo_t& t, double phis, double& pit, double& Ts) {
+  if (t.profile == 0 || t.lapse == 0.0) {
+    Ts = t.profile == 0 ? t.T0 : t.Ts0;
+    pit = std::exp(-phis / (kR * Ts));
+    return;
+  }
+  const double z = phis / kG, n = kG / (kR * t.lapse), Tz = t.Ts0 - t.lapse * z;
+  if (Tz >= t.Ttrop) {
+    Ts = Tz;
+    pit = std::pow(Tz / t.Ts0, n);
+  } else {
+    Ts = t.Ttrop;
+    const double ztr = (t.Ts0 - t.Ttrop) / t.lapse;
+    pit = std::pow(t.Ttrop / t.Ts0, n) * std::exp(-kG * (z - ztr) / (kR * t.Ttrop));
+  }
+}
+
+// beta_k, beta2, pi~ and R T~_s of a grid from its thermodynamic settings.
+static void thermo_tables(agcm_grid* g) {
+  const agcm_thermo_t& t = g->th;
+  const double kap = kR / kCp;
+  g->beta.resize(g->K);
+  for (int k = 0; k < g->K; ++k) {
+    const double mid = 0.5 * (g->sh[k] + g->sh[k + 1]);
+    g->beta[k] = (1.0 - t.delta_p) * (1.0 + t.delta_c) * std::sqrt(kap * kR * std_temperature(t, mid));
+  }
+  g->beta2 = (1.0 - t.delta_p) * t.delta * kap;
+  g->pit.resize(g->phis.size());
+  g->rts.resize(g->phis.size());
+  for (size_t n = 0; n < g->phis.size(); ++n) {
+    double Ts = 0.0;
+    std_surface(t, g->phis[n], g->pit[n], Ts);
+    g->rts[n] = kR * Ts;
+  }
+}
+
+int agcm_grid_set_thermo(agcm_grid_t* g, const agcm_thermo_t* t) {
+  if (!g) return fail(AGCM_EINVAL, "null grid");
+  if (g->dev[0].blob || g->dev[1].blob || g->refs > 0)
+    return fail(AGCM_EINVAL, "agcm_grid_set_thermo: the grid already has device tables (call it before the first state)");
+  agcm_thermo_t v{0, kT0, 288.15, 6.5e-3, 216.65, 0.0, 0.0, 0.0};
+  if (t) v = *t;
+  if ((v.profile != 0 && v.profile != 1) || !(v.T0 > 0) || !(v.Ts0 > 0) || !(v.Ttrop > 0) || v.Ttrop > v.Ts0 ||
+      !(v.lapse >= 0) || !std::isfinite(v.lapse) || !std::isfinite(v.delta) || !(v.delta_c > -1.0) ||
+      !std::isfinite(v.delta_c) || !(v.delta_p >= 0.0 && v.delta_p <= 1.0) || !std::isfinite(v.T0) ||
+      !std::isfinite(v.Ts0))
+    return fail(AGCM_EINVAL, "agcm_grid_set_thermo: value out of range");
+  g->th = v;
+  thermo_tables(g);
+  return AGCM_OK;
+}
+
 int agcm_grid_create(int nlon, int nlat, int nlev, const double* sigma_half, const int32_t* leap_u,
                      const int32_t* leap_v, const double* phis, agcm_grid_t** out) {
   if (!out) return fail(AGCM_EINVAL, "out is NULL");
@@ -553,7 +638,6 @@ int agcm_grid_create(int nlon, int nlat, int nlev, const double* sigma_half, con
   g->I = I; g->J = J; g->K = K;
   g->dlam = 2.0 * kPi / I;
   g->dth = kPi / J;
-  g->b = std::sqrt((kR / kCp) * kR * kT0);
   g->s.resize(J); g->c.resize(J); g->cot.resize(J); g->A.resize(J); g->Mu.resize(J);
   for (int j = 0; j < J; ++j) {
     const double th = (j + 0.5) * g->dth;
@@ -599,15 +683,16 @@ int agcm_grid_create(int nlon, int nlat, int nlev, const double* sigma_half, con
     g->Hkk[k] = std::log(g->sh[k + 1] / mid);
     g->hk[k] = k > 0 ? std::log(g->sh[k + 1] / g->sh[k]) : 0.0;
   }
-  g->pit.resize((size_t)J * I);
-  for (size_t n = 0; n < g->pit.size(); ++n) {
+  g->phis.assign((size_t)J * I, 0.0);
+  for (size_t n = 0; n < g->phis.size(); ++n) {
     const double p = phis ? phis[n] : 0.0;
     if (!std::isfinite(p)) {
       delete g;
       return fail(AGCM_EINVAL, "phis[%zu] is not finite", n);
     }
-    g->pit[n] = std::exp(-p / (kR * kT0));
+    g->phis[n] = p;
   }
+  thermo_tables(g);  // the default isothermal 250 K atmosphere
   *out = g;
   return AGCM_OK;
 }
@@ -631,7 +716,8 @@ int agcm_grid_leap(const agcm_grid_t* g, int32_t* lu, int32_t* lv) {
 int agcm_grid_dt(const agcm_grid_t* g, double umax, double* dt) {
   if (!g || !dt || !(umax >= 0.0)) return fail(AGCM_EINVAL, "bad argument");
   const int K = g->K;
-  // S = D^{1/2} (b^2 H D^-1 H^T D + R T0 1 1^T D) D^{-1/2}, D = diag(dsigma):
+  // S = D^{1/2} (H B^2 D^-1 H^T D + R T~_s 1 1^T D) D^{-1/2}, D = diag(dsigma),
+  // B = diag(beta_k):
   // symmetric and positive semi-definite with the eigenvalues of the column
   // operator; its largest eigenvalue by power iteration.
   std::vector<double> H((size_t)K * K, 0.0);
@@ -640,12 +726,14 @@ int agcm_grid_dt(const agcm_grid_t* g, double umax, double* dt) {
     for (int kk = k + 1; kk < K; ++kk) H[(size_t)k * K + kk] = g->hk[kk];
   }
   std::vector<double> S((size_t)K * K, 0.0);
-  const double b2 = g->b * g->b, rt = kR * kT0;
+  double rt = 0.0;
+  for (double v : g->rts) rt = std::max(rt, v);
   for (int p = 0; p < K; ++p)
     for (int q = 0; q < K; ++q) {
       double acc = 0.0;
-      for (int m = 0; m < K; ++m) acc += H[(size_t)p * K + m] * H[(size_t)q * K + m] / g->ds[m];
-      S[(size_t)p * K + q] = std::sqrt(g->ds[p] * g->ds[q]) * (b2 * acc + rt);
+      for (int m = 0; m < K; ++m)
+        acc += H[(size_t)p * K + m] * g->beta[m] * g->beta[m] * H[(size_t)q * K + m] / g->ds[m];
+      S[(size_t)p * K + q] = std::sqrt(g->ds[p] * g->ds[q]) * (acc + rt);
     }
   std::vector<double> v(K, 1.0), w(K);
   double lam = 0.0;
@@ -856,6 +944,8 @@ int agcm_step_adjoint(agcm_state_t* s, const void* const lam_in[4], void* const 
   if (!s || !lam_in || !lam_out || !std::isfinite(dt)) return fail(AGCM_EINVAL, "bad argument");
   for (int f = 0; f < 4; ++f)
     if ((!lam_in[f] || !lam_out[f]) && !(f == 1 && s->nv == 0)) return fail(AGCM_EINVAL, "null adjoint buffer %d", f);
+  if (s->grid->beta2 != 0.0 && s->grid->th.delta != 0.0)
+    return fail(AGCM_EINVAL, "the adjoint step does not cover the nonlinear delta kappa Phi/P term");
   cudaStream_t st = as_stream(stream);
   return s->prec == AGCM_FP64 ? adjoint_step<double>(s, lam_in, lam_out, dt, st)
                               : adjoint_step<float>(s, lam_in, lam_out, dt, st);
@@ -1038,14 +1128,14 @@ constexpr size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 constexpr size_t kRowB = al256(kStaticRows * 8), kLevB = al256((kStaticLevels + 1) * 8),
                  kColB = al256(kStaticCols * 8);
 constexpr size_t kOffRaw = 0;                        // 6 row arrays s c cot A sv Av (double)
-constexpr size_t kOffRawLev = kOffRaw + 6 * kRowB;   // sh ds Hkk hk (double)
-constexpr size_t kOffPitRaw = kOffRawLev + 4 * kLevB;  // pi~ (double)
-constexpr size_t kOffInt = kOffPitRaw + kColB;       // Mu Mv (int)
+constexpr size_t kOffRawLev = kOffRaw + 6 * kRowB;   // sh ds Hkk hk beta (double)
+constexpr size_t kOffPitRaw = kOffRawLev + 5 * kLevB;  // pi~, R T~_s (double)
+constexpr size_t kOffInt = kOffPitRaw + 2 * kColB;   // Mu Mv (int)
 constexpr size_t kOffRowT = kOffInt + 2 * kRowB;     // 12 typed row arrays
-constexpr size_t kOffLevT = kOffRowT + 12 * kRowB;   // 6 typed level arrays
-constexpr size_t kOffColT = kOffLevT + 6 * kLevB;    // pit, rt0pit (typed)
+constexpr size_t kOffLevT = kOffRowT + 12 * kRowB;   // 7 typed level arrays
+constexpr size_t kOffColT = kOffLevT + 7 * kLevB;    // pit, rt0pit (typed)
 constexpr size_t kOffBar = kOffColT + 2 * kColB;     // Ubar, Vbar (double)
-constexpr size_t kStaticBytes = kOffBar + 2 * kColB; // about 11 MB
+constexpr size_t kStaticBytes = kOffBar + 2 * kColB; // about 13 MB
 
 }  // namespace
 
@@ -1060,7 +1150,7 @@ void* g_static_ptr[kStaticMaxDevices] = {};
 template <class T>
 __global__ void k_static_geom(int I, int J, int K, const double* raw, const double* rawlev, const double* pitraw,
                               const int* Mu, const int* Mv, T* rowT, T* levT, T* colT, size_t rowStride,
-                              size_t levStride, size_t colStride) {
+                              size_t levStride, size_t colStride, double beta2) {
   const double* s = raw;
   const double* c = raw + rowStride;
   const double* cot = raw + 2 * rowStride;
@@ -1069,6 +1159,7 @@ __global__ void k_static_geom(int I, int J, int K, const double* raw, const doub
   const double* Av = raw + 5 * rowStride;
   const double* ds = rawlev + levStride;
   const double* hk = rawlev + 3 * levStride;
+  const double* beta = rawlev + 4 * levStride;
   const double dlam = 2.0 * kPi / I, dth = kPi / J;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   for (size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x; n < (size_t)I * J; n += stride) {
@@ -1093,13 +1184,14 @@ __global__ void k_static_geom(int I, int J, int K, const double* raw, const doub
       const int k = (int)n;
       levT[0 * levStride + k] = (T)ds[k];
       levT[1 * levStride + k] = (T)(0.5 / ds[k]);
-      levT[2 * levStride + k] = (T)hk[k];
-      levT[3 * levStride + k] = (T)rawlev[2 * levStride + k];
-      levT[4 * levStride + k] = (T)(hk[k] / ds[k]);
+      levT[2 * levStride + k] = (T)(beta[k] * hk[k]);
+      levT[3 * levStride + k] = (T)(beta[k] * rawlev[2 * levStride + k]);
+      levT[4 * levStride + k] = (T)(beta[k] * hk[k] / ds[k]);
       levT[5 * levStride + k] = (T)(1.0 - rawlev[k]);
+      levT[6 * levStride + k] = (T)(beta[k] != 0.0 ? beta2 / beta[k] : 0.0);
     }
     colT[n] = (T)pitraw[n];
-    colT[colStride + n] = (T)(kR * kT0 / pitraw[n]);
+    colT[colStride + n] = (T)(pitraw[colStride + n] / pitraw[n]);
   }
 }
 
@@ -1117,10 +1209,11 @@ int tendency_static(const agcm_grid* g, char* base, const void* U, const void* V
   for (int q = 0; q < 6; ++q)
     if (!rows[q]->empty())
       CUDA_TRY(cudaMemcpyAsync(raw + q * rS, rows[q]->data(), rows[q]->size() * 8, cudaMemcpyHostToDevice, st));
-  const std::vector<double>* levs[4] = {&g->sh, &g->ds, &g->Hkk, &g->hk};
-  for (int q = 0; q < 4; ++q)
+  const std::vector<double>* levs[5] = {&g->sh, &g->ds, &g->Hkk, &g->hk, &g->beta};
+  for (int q = 0; q < 5; ++q)
     CUDA_TRY(cudaMemcpyAsync(rawlev + q * lS, levs[q]->data(), levs[q]->size() * 8, cudaMemcpyHostToDevice, st));
   CUDA_TRY(cudaMemcpyAsync(pitraw, g->pit.data(), g->pit.size() * 8, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(pitraw + cS, g->rts.data(), g->rts.size() * 8, cudaMemcpyHostToDevice, st));
   CUDA_TRY(cudaMemcpyAsync(Mu, g->Mu.data(), g->Mu.size() * sizeof(int), cudaMemcpyHostToDevice, st));
   if (!g->Mv.empty())
     CUDA_TRY(cudaMemcpyAsync(Mv, g->Mv.data(), g->Mv.size() * sizeof(int), cudaMemcpyHostToDevice, st));
@@ -1130,7 +1223,7 @@ int tendency_static(const agcm_grid* g, char* base, const void* U, const void* V
   T* levT = (T*)(base + kOffLevT);
   T* colT = (T*)(base + kOffColT);
   k_static_geom<T><<<nblocks((size_t)I * J, 256), 256, 0, st>>>(I, J, K, raw, rawlev, pitraw, Mu, Mv, rowT, levT,
-                                                                colT, rS, lS, cS);
+                                                                colT, rS, lS, cS, g->beta2);
   agcm::Geom<T> G{};
   G.I = I; G.J = J; G.K = K;
   G.Mu = Mu;
@@ -1141,13 +1234,14 @@ int tendency_static(const agcm_grid* g, char* base, const void* U, const void* V
   G.ds = levT + 0 * lS; G.r2ds = levT + 1 * lS; G.hk = levT + 2 * lS; G.Hkk = levT + 3 * lS;
   G.hk_rds = levT + 4 * lS;
   G.oms = levT + 5 * lS;
+  G.rho = levT + 6 * lS;
+  G.nl = g->beta2 != 0.0 && g->th.delta != 0.0;
   G.dsd = rawlev + 1 * lS;
   G.shd = rawlev + 0 * lS;
   G.Ad = raw + 3 * rS;
   G.Avd = raw + 5 * rS;
   G.pit = colT;
   G.rt0pit = colT + cS;
-  G.b = (T)g->b;
   G.rady = (T)(1.0 / (kA * g->dth));
   double* ubar = (double*)(base + kOffBar);
   double* vbar = (double*)(base + kOffBar + kColB);
@@ -1290,6 +1384,10 @@ int agcm_ensemble_create(agcm_state_t* const* members, int n, agcm_ensemble_t** 
     if (!members[m] || members[m]->prec != e->prec) {
       delete e;
       return fail(AGCM_EINVAL, "member %d is null or has another precision", m);
+    }
+    if (members[m]->grid->beta2 != 0.0 && members[m]->grid->th.delta != 0.0) {
+      delete e;
+      return fail(AGCM_EINVAL, "member %d: ensembles do not cover the nonlinear delta kappa Phi/P term", m);
     }
     for (int q = 0; q < m; ++q)
       if (members[q] == members[m]) {

@@ -33,9 +33,12 @@ struct Geom {
   // levels
   const T* ds;      // dsigma_k (K)
   const T* r2ds;    // 1 / (2 dsigma_k) (K)
-  const T* hk;      // H[k'][k'] off-diagonal weight ln(sh_{k+1}/sh_k), hk[0] = 0 (K)
-  const T* Hkk;     // diagonal ln(sh_{k+1}/sigma_k) (K)
+  // hydrostatic weights times the level coefficient beta_k = (1 - delta_p)
+  // (1 + delta_c) b_k of Eq. 1 (b_k = sqrt(kappa R T~(sigma_k))):
+  const T* hk;      // beta_k ln(sh_{k+1}/sh_k), the off-diagonal weight; hk[0] = 0 (K)
+  const T* Hkk;     // beta_k ln(sh_{k+1}/sigma_k), the diagonal (K)
   const T* hk_rds;  // hk / dsigma_k (K)
+  const T* rho;     // beta2 / beta_k: the delta kappa Phi/P part of the coefficient (K)
   const T* oms;     // 1 - sigma_hat_k (K): W_k = SD_k - (1 - sigma_hat_k) C
   // rows the low-latitude filter changes, entry 4 j + band (1 two-grid, 2 3-point)
   const int* filtU; // scalar / U rows
@@ -46,9 +49,9 @@ struct Geom {
   const double* Ad;   // A_j in FP64 (J)     (diagnostics)
   const double* Avd;  // Av_j in FP64 (J-1)  (diagnostics)
   // columns (J*I)
-  const T* rt0pit;  // R T0 / pi~
-  const T* pit;     // pi~ = exp(-phi_s / (R T0))
-  T b;              // sqrt(kappa R T0)
+  const T* rt0pit;  // R T~_s / pi~
+  const T* pit;     // pi~: standard surface pressure / p0 under phi_s
+  int nl;           // 1: the delta kappa Phi/P term is on (beta2 != 0)
   T rady;           // 1 / (a dth)
 };
 

@@ -159,7 +159,7 @@ __device__ __forceinline__ void tile_issue(const TileCtx<T>& t, const Geom<T>& g
 // TERMS selects the term groups of Eq. 2: 1 = advection L (skew flux form,
 // vertical advection), 2 = adaptation A (pressure gradient, Coriolis pair,
 // Omega~ conversion, dpi/dt), 3 = both (the unsplit step).
-template <class T, int MODE, bool TILE, int TERMS = 3>
+template <class T, int MODE, bool TILE, int TERMS = 3, bool NL = false>
 __device__ __forceinline__ void fused_column(
     const Geom<T>& g, const int i, const int j, const T* __restrict__ U, const T* __restrict__ V,
     const T* __restrict__ Phi, const T* __restrict__ pi, const double* __restrict__ Ubar,
@@ -260,7 +260,7 @@ __device__ __forceinline__ void fused_column(
     f0s = g.f0[j + 1];
     cotas = g.cota[j + 1];
   }
-  const T b = g.b, rady = g.rady;
+  const T rady = g.rady;
 
   // ---- column integrals C (FP64) at the own column, i+1 and j+1
   const double Cc = ((double)PufE * Ubar[rj + fE] - (double)PufW * Ubar[rj + fW]) * (double)rdx +
@@ -305,6 +305,7 @@ __device__ __forceinline__ void fused_column(
   // that level is completed and written
   T q_ds = g.ds[K - 1], q_H = g.Hkk[K - 1], q_hk = g.hk[K - 1], q_hr = g.hk_rds[K - 1], q_r2 = g.r2ds[K - 1];
   T q_om = g.oms[K - 1];
+  T q_rho = NL ? g.rho[K - 1] : T(0);
   double q_dsd = g.dsd[K - 1];
   T p_r2 = 0, p_ds = 0;   // level below: 1/(2 dsigma), dsigma
   double p_dsd = 0.0;
@@ -339,7 +340,7 @@ __device__ __forceinline__ void fused_column(
         Phk = Phi + (size_t)k * plane;
         Vk = V + (size_t)k * vplane;
       }
-      const T dsk = q_ds, Hkk = q_H, hk = q_hk, hkr = q_hr, r2dsk = q_r2, onems = q_om;
+      const T dsk = q_ds, Hkk = q_H, hk = q_hk, hkr = q_hr, r2dsk = q_r2, onems = q_om, rho = q_rho;
       c_r2 = q_r2;
       c_ds = q_ds;
       c_dsd = q_dsd;
@@ -350,6 +351,7 @@ __device__ __forceinline__ void fused_column(
         q_hr = g.hk_rds[k - 1];
         q_r2 = g.r2ds[k - 1];
         q_om = g.oms[k - 1];
+        if (NL) q_rho = g.rho[k - 1];
         q_dsd = g.dsd[k - 1];
       }
       // loads
@@ -398,7 +400,9 @@ __device__ __forceinline__ void fused_column(
         T hor = zf * (FlE * Phe * rPe - FlW * Phw * rPw);
         if (hasS) hor += yvj * Ftc * Phs * rPs;
         if (hasN) hor -= yvjm * Ftn * Phn * rPn;
-        const T X = -(b * rPc) * (Hkk * D + hkr * (Cf - SD));
+        // Omega~ with Eq. 1's coefficient: Hkk, hkr carry beta_k; the
+        // delta kappa Phi/P part scales it by 1 + rho_k Phi/P
+        const T X = -(NL ? rPc * (one + rho * Gsc) : rPc) * (Hkk * D + hkr * (Cf - SD));
         nPPh = (ADA ? X : T(0)) - (ADV ? (hor * r2A + Wb * GsB * r2dsk) * rPc : T(0));
       }
       // ---- U cell
@@ -410,7 +414,11 @@ __device__ __forceinline__ void fused_column(
         if (hasN) hor -= T(0.5) * yvjm * (Ftn + Ftnp) * Un * rPun;
         const T WuB = T(0.5) * (Wb + Wbp);
         // a5/a6: psi difference over the (x+N, x-N+1) pair
-        const T BE1 = b * rPE1 * PhE1, BW1 = b * rPW1 * PhW1;
+        T BE1 = rPE1 * PhE1, BW1 = rPW1 * PhW1;
+        if (NL) {
+          BE1 *= one + rho * BE1;
+          BW1 *= one + rho * BW1;
+        }
         const T dpsi = Hkk * (BE1 - BW1) + dSU + (psE1 - psW1);
         dSU += hk * (BE1 - BW1);
         const T pgf = Puc * dpsi * rdx;
@@ -429,7 +437,11 @@ __device__ __forceinline__ void fused_column(
         if (hasSS) hor += T(0.5) * (yvj * Ftc + yvjp * Fts) * Vs * rPvs;
         if (hasN) hor -= T(0.5) * (yvjm * Ftn + yvj * Ftc) * Vn * rPvn;
         const T WvB = T(0.5) * (Wb + Wbs);
-        const T Bs = b * rPs * Phs, Bc = b * rPc * Phc;
+        T Bs = rPs * Phs, Bc = Gsc;
+        if (NL) {
+          Bs *= one + rho * Bs;
+          Bc *= one + rho * Bc;
+        }
         const T dpsi = Hkk * (Bs - Bc) + dSV + (pss - psc);
         dSV += hk * (Bs - Bc);
         const T pgf = Pvc * dpsi * rady;
@@ -499,7 +511,7 @@ __device__ __forceinline__ void fused_column(
 // global memory (the row index is warp-uniform, so row tables sit in uniform
 // registers).  BY = kTileY: a 32 x 4 tile whose levels are staged in shared
 // memory by the TMA bulk-copy engine (global loads where the halo is too wide).
-template <class T, int MODE, int BY, int TERMS = 3>
+template <class T, int MODE, int BY, int TERMS = 3, bool NL = false>
 __global__ void __launch_bounds__(kTileX* BY, BY == 1 ? (sizeof(T) == 4 ? AGCM_FUSED_MINB : AGCM_FUSED_MINB64)
                                                       : (sizeof(T) == 4 ? AGCM_TILE_MINB : 2))
     k_fused_stage(Geom<T> g, const T* __restrict__ U, const T* __restrict__ V, const T* __restrict__ Phi,
@@ -511,7 +523,7 @@ __global__ void __launch_bounds__(kTileX* BY, BY == 1 ? (sizeof(T) == 4 ? AGCM_F
   if (BY == 1) {
     const int i = blockIdx.x * kTileX + tx, j = blockIdx.y;
     if (i < g.I)
-      fused_column<T, MODE, false, TERMS>(g, i, j, U, V, Phi, pi, Ubar, Vbar, Ub, Vb, Phib, pib, Uo, Vo, Phio, pio, Ubar_o,
+      fused_column<T, MODE, false, TERMS, NL>(g, i, j, U, V, Phi, pi, Ubar, Vbar, Ub, Vb, Phib, pib, Uo, Vo, Phio, pio, Ubar_o,
                                    Vbar_o, Ubar_b, Vbar_b, cdt);
     return;
   }

@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(128) k_column(Geom<T> g, const T* __restrict__
   const double pb = pi_base ? (double)pi_base[n] : 0.0;
   pi_out[n] = (T)(pb - cdt * C);
   // pass 2: prefix sum from the top -> W at half levels and the Omega~ term
-  const T bP = g.b * cs.rP[n];
+  const T bP = cs.rP[n];  // the level coefficient sits in the H tables
   double Q = 0.0;
   W[n] = T(0);
   for (int k = 0; k < K; ++k) {
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(128) k_column(Geom<T> g, const T* __restrict__
     Q += g.dsd[k] * (double)D;
   }
   W[(size_t)K * plane + n] = T(0);
-  // pass 3: suffix sum from the surface -> phi' + R T0 pi / pi~
+  // pass 3: suffix sum from the surface -> phi' + R T~_s pi / pi~
   const T ps = g.rt0pit[n] * pi[n];
   T S = T(0);
   for (int k = K - 1; k >= 0; --k) {

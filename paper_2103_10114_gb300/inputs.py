@@ -1,7 +1,8 @@
 """Seeded synthetic inputs shared by the tests, the smoke check and the bench.
 
 This module holds no arithmetic of the dynamical core.  It only lays closed-form
-or random fields on the grid points (reading R1 of the design notes):
+or random fields on the grid points of the pole-free offset grid (the paper's
+720 x 361 counts imply pole rows; this grid has none):
 
 * scalar / Phi / pi points at longitude ``i*dlam`` and colatitude ``(j+1/2)*dth``;
 * U points at longitude ``(i+1/2)*dlam`` on the scalar rows;
@@ -14,7 +15,7 @@ IAP units of m/s, pi = p'_sa/p0), float64, storage ``[k][j][i]``.
 
 The paper names its workloads (the Rossby-Haurwitz wave test and F_2000 runs,
 Sec. "Validation of AGCM-3DLF") but prints no constants for them; the
-amplitudes below are this project's choices and are listed in the design notes.
+amplitudes below are this project's choices; each is stated where it is set.
 """
 from __future__ import annotations
 

@@ -108,3 +108,41 @@ def test_split_dt_rule(L):
     want = 1.6 / (100.0 * math.hypot(2 / (a * math.cos(math.pi / 4) * dl), 2 / (a * dth)))
     assert abs(dt / want - 1) < 1e-12
     assert dt / m <= g.dt(0.0) * (1 + 1e-12) and dt / (m - 1) > g.dt(0.0)
+
+
+def test_thermo_dt_and_validation(L):
+    """With a lapse-rate standard atmosphere and Eq. 1's delta_c, delta_p the
+    dt rule weights each level's hydrostatic coupling by
+    (1 - delta_p)(1 + delta_c) sqrt(kappa R T~(sigma_k)) and uses the largest
+    R T~_s; the numpy eigenproblem below is written from that statement."""
+    I, J, K = 128, 64, 30
+    rng = np.random.default_rng(2)
+    phis = np.abs(rng.normal(0, 5e3, (J, I)))
+    th = dict(profile=1, Ts0=288.15, lapse=6.5e-3, Ttrop=216.65, delta_c=0.3, delta_p=0.2)
+    g = agcm.Grid(I, J, K, phis=phis, thermo=th)
+    R, cp, G0 = 287.04, 1004.64, 9.80665
+    sh = np.arange(K + 1) / K
+    ds, mid = np.diff(sh), 0.5 * (sh[:-1] + sh[1:])
+    T = np.maximum(288.15 * mid ** (R * 6.5e-3 / G0), 216.65)
+    beta = 0.8 * 1.3 * np.sqrt((R / cp) * R * T)
+    H = np.zeros((K, K))
+    for k in range(K):
+        H[k, k] = math.log(sh[k + 1] / mid[k])
+        for kk in range(k + 1, K):
+            H[k, kk] = math.log(sh[kk + 1] / sh[kk])
+    Ts = 288.15 - 6.5e-3 * phis / G0
+    N = H @ np.diag(beta**2 / ds) @ H.T @ np.diag(ds) + R * Ts.max() * np.outer(np.ones(K), ds)
+    cmax = math.sqrt(max(np.linalg.eigvals(N).real))
+    a = 6.371e6
+    dl, dth = 2 * math.pi / I, math.pi / J
+    want = 1.6 / ((cmax + 100.0) * math.hypot(2 / (a * math.cos(math.pi / 4) * dl), 2 / (a * dth)))
+    assert abs(g.dt(100.0) / want - 1) < 1e-10
+    # defaults restored by an explicit default
+    g2 = agcm.Grid(I, J, K, phis=phis)
+    g.set_thermo()
+    assert abs(g.dt(100.0) / g2.dt(100.0) - 1) < 1e-14
+    for bad in (dict(profile=3), dict(T0=0.0), dict(delta_p=-0.1), dict(delta_c=-1.0), dict(Ttrop=400.0),
+                dict(lapse=float("nan")), dict(delta=float("inf"))):
+        with pytest.raises(agcm.AgcmError) as e:
+            g.set_thermo(**bad)
+        assert e.value.code == agcm.AGCM_EINVAL

@@ -59,3 +59,27 @@ def test_static_tendency_rejects_oversized_grid():
     rc = agcm.lib().agcm_tendency_static(g.handle, agcm.AGCM_FP32, *([ctypes.c_void_p(16)] * 8), None)
     assert rc == agcm.AGCM_EINVAL
     assert "static scratch limit" in agcm.lib().agcm_last_error().decode()
+
+
+@pytest.mark.parametrize("precision,tol", [(agcm.AGCM_FP64, 1e-12), (agcm.AGCM_FP32, 1e-6)])
+def test_static_tendency_with_thermodynamics(cuda_ok, precision, tol):
+    """The static path builds its own level tables: the lapse-rate profile with
+    the nonlinear delta term gives the same tendency as the state path."""
+    import torch
+
+    agcm.build()
+    I, J, K = 64, 32, 10
+    st = inputs.baroclinic_jet(I, J, K, seed=5, noise=1e-2, terrain_seed=2)
+    th = dict(profile=1, Ts0=288.15, lapse=6.5e-3, Ttrop=216.65, delta=1.0, delta_c=0.3, delta_p=0.2)
+    g = agcm.Grid(I, J, K, phis=st["phis"], thermo=th)
+    s = agcm.State(g, precision)
+    dev_in = {f: torch.as_tensor(np.ascontiguousarray(st[f]), dtype=s.dtype, device="cuda") for f in FIELDS}
+    s.load(dev_in)
+    ref = s.tendency()
+    got = _static_tendency(g, precision, dev_in)
+    torch.cuda.synchronize()
+    for f in FIELDS:
+        r, o = ref[f].double().cpu().numpy(), got[f].double().cpu().numpy()
+        assert np.abs(o - r).max() / max(np.abs(r).max(), 1e-300) <= tol, f
+    s.close()
+    g.close()

@@ -43,7 +43,7 @@ NCU_TRAFFIC = {
 # (fadd + fmul + 2 ffma), thread instructions per point, warp instructions
 # issued per point.
 NCU_OPS = {
-    "k_fused_stage": ("c3e706169b73c2f492ce566441542579c37deeaa", 228.8, 528.4, 16.9,
+    "k_fused_stage": ("12115a8f7b72f7d17ac9d262e1df687839159e67", 225.7, 527.1, 16.84,
                       "profiles/fused_stage_ops_720x360x30_fp32.md"),
 }
 

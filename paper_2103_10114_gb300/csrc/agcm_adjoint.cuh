@@ -43,21 +43,27 @@ __device__ __forceinline__ void aadd(T* p, T v) {
 
 // Reverse of phase C at (k, j, i): U point (j, u = i), Phi point, V point.
 template <class T>
-__global__ void __launch_bounds__(256) k_adj_update(Geom<T> g, const T* __restrict__ U, const T* __restrict__ V,
-                                                    const T* __restrict__ Phi, ColState<T> cs,
-                                                    const T* __restrict__ W, const T* __restrict__ psi,
-                                                    const T* __restrict__ yU, const T* __restrict__ yV,
-                                                    const T* __restrict__ yPhi, AdjBufs<T> a) {
+__device__ __forceinline__ void adj_update_point(
+    const Geom<T>& g, const T* __restrict__ U, const T* __restrict__ V, const T* __restrict__ Phi,
+    const T* __restrict__ Pu, const T* __restrict__ rPu, const T* __restrict__ Pv, const T* __restrict__ rPv,
+    const T* __restrict__ rP, const T* __restrict__ W, const T* __restrict__ psi, const T* __restrict__ yU,
+    const T* __restrict__ yV, const T* __restrict__ yPhi, const AdjBufs<T>& a, const int k, const int j,
+    const int i) {
+  // every input is read-only here and every output is written with atomics
+  // or plain stores to other arrays, so the reads are declared restrict and
+  // the row tables read once, letting loads move ahead of the atomics
   const int I = g.I, J = g.J, K = g.K;
-  const size_t N = (size_t)K * J * I;
-  const size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= N) return;
-  const int i = (int)(n % I);
-  const size_t kj = n / I;
-  const int j = (int)(kj % J), k = (int)(kj / J);
+  const bool hasS_ = j < J - 1, hasN_ = j > 0, hasSS_ = j + 1 < J - 1;
+  const T yvj = hasS_ ? g.yv[j] : T(0), yvjm = hasN_ ? g.yv[j - 1] : T(0), yvjp = hasSS_ ? g.yv[j + 1] : T(0);
+  const T r2Aj = g.r2A[j], r2dsk = g.r2ds[k], rdxj = g.rdx[j], f0j = g.f0[j], cotaj = g.cota[j];
+  const T zfvj = hasS_ ? g.zfv[j] : T(0), r2Avj = hasS_ ? g.r2Av[j] : T(0);
+  const T cnj = hasS_ ? g.cn[j] : T(0), csj = hasS_ ? g.cs[j] : T(0);
+  const T f0j1 = hasS_ ? g.f0[j + 1] : T(0), cotaj1 = hasS_ ? g.cota[j + 1] : T(0);
+  const int Mvj = hasS_ ? g.Mv[j] : 1;
+  const T rady = g.rady;
+  const size_t n = ((size_t)k * J + j) * I + i;
   const size_t plane = (size_t)J * I, vplane = (size_t)(J - 1) * I;
   const size_t r3 = ((size_t)k * J + j) * I, r2 = (size_t)j * I, rv = ((size_t)k * (J - 1) + j) * I;
-  const T *Pu = cs.Pu, *rPu = cs.rPu, *Pv = cs.Pv, *rPv = cs.rPv, *rP = cs.rP;
   const bool hasS = j < J - 1, hasN = j > 0;
   const int M = g.Mu[j];
   const T zf = g.zf[j];
@@ -76,12 +82,12 @@ __global__ void __launch_bounds__(256) k_adj_update(Geom<T> g, const T* __restri
     if (hasS) {
       Gs_s = Phi[r3 + I + i] * rP[r2 + I + i];
       Ft_c = Ft(rv, r2, i);
-      hor += g.yv[j] * Ft_c * Gs_s;
+      hor += yvj * Ft_c * Gs_s;
     }
     if (hasN) {
       Gs_n = Phi[r3 - I + i] * rP[r2 - I + i];
       Ft_n = Ft(rv - I, r2 - I, i);
-      hor -= g.yv[j - 1] * Ft_n * Gs_n;
+      hor -= yvjm * Ft_n * Gs_n;
     }
     const T rPc = rP[r2 + i];
     T ver = 0, Wb = 0, Wt = 0, Gb = 0, Gt = 0;
@@ -97,19 +103,19 @@ __global__ void __launch_bounds__(256) k_adj_update(Geom<T> g, const T* __restri
     }
     // T = -(hor r2A + ver r2ds) rPc + X
     const T Lb = -yb;
-    const T hb = Lb * g.r2A[j] * rPc, vb = Lb * g.r2ds[k] * rPc;
-    a.tRP[n] = Lb * (hor * g.r2A[j] + ver * g.r2ds[k]);
+    const T hb = Lb * r2Aj * rPc, vb = Lb * r2dsk * rPc;
+    a.tRP[n] = Lb * (hor * r2Aj + ver * r2dsk);
     aadd(a.aFl + r3 + fE, zf * hb * Ge);
     aadd(a.aFl + r3 + fW, -zf * hb * Gw);
     aadd(a.aGs + r3 + ie, hb * ZE);
     aadd(a.aGs + r3 + iw, -hb * ZW);
     if (hasS) {
-      aadd(a.aFt + rv + i, hb * g.yv[j] * Gs_s);
-      aadd(a.aGs + r3 + I + i, hb * g.yv[j] * Ft_c);
+      aadd(a.aFt + rv + i, hb * yvj * Gs_s);
+      aadd(a.aGs + r3 + I + i, hb * yvj * Ft_c);
     }
     if (hasN) {
-      aadd(a.aFt + rv - I + i, -hb * g.yv[j - 1] * Gs_n);
-      aadd(a.aGs + r3 - I + i, -hb * g.yv[j - 1] * Ft_n);
+      aadd(a.aFt + rv - I + i, -hb * yvjm * Gs_n);
+      aadd(a.aGs + r3 - I + i, -hb * yvjm * Ft_n);
     }
     if (k < K - 1) {
       aadd(a.aW + (size_t)(k + 1) * plane + r2 + i, vb * Gb);
@@ -133,12 +139,12 @@ __global__ void __launch_bounds__(256) k_adj_update(Geom<T> g, const T* __restri
     T hor = ZE * Ge - ZW * Gw;
     T YS = 0, YN = 0, Gs_ = 0, Gn_ = 0;
     if (hasS) {
-      YS = T(0.5) * g.yv[j] * (Ft(rv, r2, u) + Ft(rv, r2, up));
+      YS = T(0.5) * yvj * (Ft(rv, r2, u) + Ft(rv, r2, up));
       Gs_ = U[r3 + I + u] * rPu[r2 + I + u];
       hor += YS * Gs_;
     }
     if (hasN) {
-      YN = T(0.5) * g.yv[j - 1] * (Ft(rv - I, r2 - I, u) + Ft(rv - I, r2 - I, up));
+      YN = T(0.5) * yvjm * (Ft(rv - I, r2 - I, u) + Ft(rv - I, r2 - I, up));
       Gn_ = U[r3 - I + u] * rPu[r2 - I + u];
       hor -= YN * Gn_;
     }
@@ -160,19 +166,19 @@ __global__ void __launch_bounds__(256) k_adj_update(Geom<T> g, const T* __restri
     const T Puc = Pu[r2 + u];
     const T Uc = U[r3 + u];
     const T Gc = Uc * rPc;
-    const T fs = g.f0[j] + Gc * g.cota[j];
+    const T fs = f0j + Gc * cotaj;
     T vs = 0;
     if (hasN) vs += V[rv - I + u] + V[rv - I + up];
     if (hasS) vs += V[rv + u] + V[rv + up];
     // T = -(hor r2A + ver r2ds) rPu - Pu dpsi rdx - 1/4 fs vs
     const T Lb = -yb;
-    const T hb = Lb * g.r2A[j] * rPc, vb = Lb * g.r2ds[k] * rPc;
-    a.tRPu[n] = Lb * (hor * g.r2A[j] + ver * g.r2ds[k]);
-    a.tPu[n] = -yb * dpsi * g.rdx[j];
-    aadd(a.aPsi + r3 + fE1, -yb * Puc * g.rdx[j]);
-    aadd(a.aPsi + r3 + fW1, yb * Puc * g.rdx[j]);
+    const T hb = Lb * r2Aj * rPc, vb = Lb * r2dsk * rPc;
+    a.tRPu[n] = Lb * (hor * r2Aj + ver * r2dsk);
+    a.tPu[n] = -yb * dpsi * rdxj;
+    aadd(a.aPsi + r3 + fE1, -yb * Puc * rdxj);
+    aadd(a.aPsi + r3 + fW1, yb * Puc * rdxj);
     const T fsb = -T(0.25) * yb * vs, vsb = -T(0.25) * yb * fs;
-    aadd(a.aGu + r3 + u, fsb * g.cota[j]);
+    aadd(a.aGu + r3 + u, fsb * cotaj);
     if (hasN) {
       aadd(a.aV + rv - I + u, vsb);
       aadd(a.aV + rv - I + up, vsb);
@@ -191,14 +197,14 @@ __global__ void __launch_bounds__(256) k_adj_update(Geom<T> g, const T* __restri
     if (hasS) {
       const T YSb = hb * Gs_;
       aadd(a.aGu + r3 + I + u, hb * YS);
-      aadd(a.aFt + rv + u, T(0.5) * g.yv[j] * YSb);
-      aadd(a.aFt + rv + up, T(0.5) * g.yv[j] * YSb);
+      aadd(a.aFt + rv + u, T(0.5) * yvj * YSb);
+      aadd(a.aFt + rv + up, T(0.5) * yvj * YSb);
     }
     if (hasN) {
       const T YNb = -hb * Gn_;
       aadd(a.aGu + r3 - I + u, -hb * YN);
-      aadd(a.aFt + rv - I + u, T(0.5) * g.yv[j - 1] * YNb);
-      aadd(a.aFt + rv - I + up, T(0.5) * g.yv[j - 1] * YNb);
+      aadd(a.aFt + rv - I + u, T(0.5) * yvjm * YNb);
+      aadd(a.aFt + rv - I + up, T(0.5) * yvjm * YNb);
     }
     if (k < K - 1) {
       const size_t wb = (size_t)(k + 1) * plane + r2;
@@ -217,8 +223,8 @@ __global__ void __launch_bounds__(256) k_adj_update(Geom<T> g, const T* __restri
   if (hasS) {
     const size_t nv = rv + i;
     const T yb = yV[nv];
-    const int Mv = g.Mv[j];
-    const T zfv = g.zfv[j];
+    const int Mv = Mvj;
+    const T zfv = zfvj;
     const int uE = wrapi(i + (Mv - 1) / 2, I), uW = wrapi(i - (Mv + 1) / 2, I);
     const int ie = wrapi(i + Mv, I), iw = wrapi(i - Mv, I);
     const T ZE = zfv * T(0.5) * (Fl(r3, r2, uE) + Fl(r3 + I, r2 + I, uE));
@@ -229,12 +235,12 @@ __global__ void __launch_bounds__(256) k_adj_update(Geom<T> g, const T* __restri
     T YS = 0, YN = 0, Gs_ = 0, Gn_ = 0;
     const bool hasSS = j + 1 < J - 1;
     if (hasSS) {
-      YS = T(0.5) * (g.yv[j] * Fc + g.yv[j + 1] * Ft(rv + I, r2 + I, i));
+      YS = T(0.5) * (yvj * Fc + yvjp * Ft(rv + I, r2 + I, i));
       Gs_ = V[rv + I + i] * rPv[r2 + I + i];
       hor += YS * Gs_;
     }
     if (hasN) {
-      YN = T(0.5) * (g.yv[j - 1] * Ft(rv - I, r2 - I, i) + g.yv[j] * Fc);
+      YN = T(0.5) * (yvjm * Ft(rv - I, r2 - I, i) + yvj * Fc);
       Gn_ = V[rv - I + i] * rPv[r2 - I + i];
       hor -= YN * Gn_;
     }
@@ -256,24 +262,25 @@ __global__ void __launch_bounds__(256) k_adj_update(Geom<T> g, const T* __restri
     const T Pvc = Pv[r2 + i];
     // T = -(hor r2Av + ver r2ds) rPv - Pv dpsi rady + cor
     const T Lb = -yb;
-    const T hb = Lb * g.r2Av[j] * rPc, vb = Lb * g.r2ds[k] * rPc;
-    a.tRPv[nv] = Lb * (hor * g.r2Av[j] + ver * g.r2ds[k]);
-    a.tPv[nv] = -yb * dpsi * g.rady;
-    aadd(a.aPsi + r3 + I + i, -yb * Pvc * g.rady);
-    aadd(a.aPsi + r3 + i, yb * Pvc * g.rady);
+    const T hb = Lb * r2Avj * rPc, vb = Lb * r2dsk * rPc;
+    a.tRPv[nv] = Lb * (hor * r2Avj + ver * r2dsk);
+    a.tPv[nv] = -yb * dpsi * rady;
+    aadd(a.aPsi + r3 + I + i, -yb * Pvc * rady);
+    aadd(a.aPsi + r3 + i, yb * Pvc * rady);
     // Coriolis: cor = cn (fU(j,im) + fU(j,i)) + cs (fU(j+1,im) + fU(j+1,i)),
     // fU = (f0 + G cota) U with G = U / P^u:  dU += c (f0 + G cota), dG += c U cota
     const int im = wrapi(i - 1, I);
     auto corb = [&](size_t row3, int jj, int uu, T c) {
+      const T f0r = jj == j ? f0j : f0j1, cotar = jj == j ? cotaj : cotaj1;
       const T Uv = U[row3 + uu];
       const T Gv_ = Uv * rPu[(size_t)jj * I + uu];
-      aadd(a.aU + row3 + uu, c * (g.f0[jj] + Gv_ * g.cota[jj]));
-      aadd(a.aGu + row3 + uu, c * Uv * g.cota[jj]);
+      aadd(a.aU + row3 + uu, c * (f0r + Gv_ * cotar));
+      aadd(a.aGu + row3 + uu, c * Uv * cotar);
     };
-    corb(r3, j, im, yb * g.cn[j]);
-    corb(r3, j, i, yb * g.cn[j]);
-    corb(r3 + I, j + 1, im, yb * g.cs[j]);
-    corb(r3 + I, j + 1, i, yb * g.cs[j]);
+    corb(r3, j, im, yb * cnj);
+    corb(r3, j, i, yb * cnj);
+    corb(r3 + I, j + 1, im, yb * csj);
+    corb(r3 + I, j + 1, i, yb * csj);
     // advection
     const T ZEb = hb * Ge, ZWb = -hb * Gw;
     aadd(a.aGv + rv + ie, hb * ZE);
@@ -285,14 +292,14 @@ __global__ void __launch_bounds__(256) k_adj_update(Geom<T> g, const T* __restri
     if (hasSS) {
       const T YSb = hb * Gs_;
       aadd(a.aGv + rv + I + i, hb * YS);
-      aadd(a.aFt + rv + i, T(0.5) * g.yv[j] * YSb);
-      aadd(a.aFt + rv + I + i, T(0.5) * g.yv[j + 1] * YSb);
+      aadd(a.aFt + rv + i, T(0.5) * yvj * YSb);
+      aadd(a.aFt + rv + I + i, T(0.5) * yvjp * YSb);
     }
     if (hasN) {
       const T YNb = -hb * Gn_;
       aadd(a.aGv + rv - I + i, -hb * YN);
-      aadd(a.aFt + rv - I + i, T(0.5) * g.yv[j - 1] * YNb);
-      aadd(a.aFt + rv + i, T(0.5) * g.yv[j] * YNb);
+      aadd(a.aFt + rv - I + i, T(0.5) * yvjm * YNb);
+      aadd(a.aFt + rv + i, T(0.5) * yvj * YNb);
     }
     if (k < K - 1) {
       const size_t wb = (size_t)(k + 1) * plane + r2;
@@ -307,6 +314,23 @@ __global__ void __launch_bounds__(256) k_adj_update(Geom<T> g, const T* __restri
       aadd(a.aGv + rv - vplane + i, -vb * WT);
     }
   }
+}
+
+// One thread per column of a kAdjTileX x kAdjTileY tile, levels in a loop (at
+// most 102 registers: 5 blocks per SM):
+// the 2-D factors of a column and the level above and below are re-read from
+// L1 instead of from other SMs' working sets.
+constexpr int kAdjTileX = 32, kAdjTileY = 4;
+template <class T>
+__global__ void __launch_bounds__(kAdjTileX* kAdjTileY, 5) k_adj_update(
+    Geom<T> g, const T* __restrict__ U, const T* __restrict__ V, const T* __restrict__ Phi, ColState<T> cs,
+    const T* __restrict__ W, const T* __restrict__ psi, const T* __restrict__ yU, const T* __restrict__ yV,
+    const T* __restrict__ yPhi, AdjBufs<T> a) {
+  const int i = blockIdx.x * kAdjTileX + (int)(threadIdx.x % kAdjTileX);
+  const int j = blockIdx.y * kAdjTileY + (int)(threadIdx.x / kAdjTileX);
+  if (i >= g.I || j >= g.J) return;
+  for (int k = 0; k < g.K; ++k)
+    adj_update_point<T>(g, U, V, Phi, cs.Pu, cs.rPu, cs.Pv, cs.rPv, cs.rP, W, psi, yU, yV, yPhi, a, k, j, i);
 }
 
 // Reverse of phase B, one thread per column.  Forward (per column):

@@ -1054,7 +1054,9 @@ int vjp(agcm_state* s, void* const x[4], const void* const y[4], void* const out
   for (int q : {0, 1, 2}) CUDA_TRY(cudaMemsetAsync(s->adjv[q], 0, std::max<size_t>(nv, 1) * e, st));
   CUDA_TRY(cudaMemsetAsync(s->adjW, 0, (size_t)(G.K + 1) * n2 * e, st));
   s->prof.begin(KID_ADJ_UPDATE, st);
-  agcm::k_adj_update<T><<<nblocks(n3, 256), 256, 0, st>>>(G, (const T*)x[0], (const T*)x[1], (const T*)x[2], cs,
+  const dim3 agrid((unsigned)((G.I + agcm::kAdjTileX - 1) / agcm::kAdjTileX),
+                   (unsigned)((G.J + agcm::kAdjTileY - 1) / agcm::kAdjTileY));
+  agcm::k_adj_update<T><<<agrid, agcm::kAdjTileX * agcm::kAdjTileY, 0, st>>>(G, (const T*)x[0], (const T*)x[1], (const T*)x[2], cs,
                                                           (const T*)s->W, (const T*)s->psi, (const T*)y[0],
                                                           (const T*)y[1], (const T*)y[2], a);
   s->prof.end(st);

@@ -349,43 +349,47 @@ __global__ void __launch_bounds__(128) k_adj_column(Geom<T> g, const T* __restri
   if (n >= I * J) return;
   const int j = n / I, i = n - j * I;
   const size_t plane = (size_t)J * I;
-  const T rPc = cs.rP[n];
+  const T rPc = ldg(cs.rP + n);
   const T bP = rPc;  // the level coefficient sits in the H tables
   // C-bar = -ypi + sum_h sh_h Wbar_h
-  double Cb = -(double)ypi[n];
-  for (int h = 1; h < K; ++h) Cb += g.shd[h] * (double)a.aW[(size_t)h * plane + n];
+  double Cb = -(double)ldg(ypi + n);
+  for (int h = 1; h < K; ++h) Cb += ldg(g.shd + h) * (double)ldg(a.aW + (size_t)h * plane + n);
   // psi: Bbar_k = Hkk psibar_k + h_k sum_{k'<k} psibar_k' (prefix from the top)
   T pre = 0, psum = 0, arp = 0;
   for (int k = 0; k < K; ++k) {
-    const T pb = a.aPsi[(size_t)k * plane + n];
-    const T Bb = g.Hkk[k] * pb + g.hk[k] * pre;
+    const T pb = ldg(a.aPsi + (size_t)k * plane + n);
+    const T Bb = ldg(g.Hkk + k) * pb + ldg(g.hk + k) * pre;
     pre += pb;
     psum += pb;
-    const T ph = Phi[(size_t)k * plane + n];
+    const T ph = ldg(Phi + (size_t)k * plane + n);
     a.aPhi[(size_t)k * plane + n] = Bb * bP;
     arp += Bb * ph;
   }
   // X: dX_k/drP = X_k / rP
-  for (int k = 0; k < K; ++k) arp += yPhi[(size_t)k * plane + n] * X[(size_t)k * plane + n] / rPc;
+  for (int k = 0; k < K; ++k) arp += ldg(yPhi + (size_t)k * plane + n) * ldg(X + (size_t)k * plane + n) / rPc;
   a.arPcol[n] = arp;
-  a.aPiD[n] = psum * g.rt0pit[n];
+  a.aPiD[n] = psum * ldg(g.rt0pit + n);
   // Dbar_k = ds_k (Cb - sum_{h>k} Wbar_h) - bP ds_k (Hkk Xbar_k / ds_k + sum_{k'>k} h_k' Xbar_k' / ds_k')
-  const int M = g.Mu[j];
+  const int M = ldg(g.Mu + j);
   const int fE = wrapi(i + (M - 1) / 2, I), fW = wrapi(i - (M + 1) / 2, I);
+  // the inputs are read through the read-only path so that the reads of a
+  // level need not wait behind the previous level's atomics
+  const T rdxj = ldg(g.rdx + j), rdyj = ldg(g.rdy + j);
+  const T csS = j < J - 1 ? ldg(g.sv + j) * rdyj : T(0), csN = j > 0 ? ldg(g.sv + j - 1) * rdyj : T(0);
   double SW = 0.0;
   T SX = 0;
   for (int k = K - 1; k >= 0; --k) {
-    const T xb = yPhi[(size_t)k * plane + n];
-    const T ds = g.ds[k];
-    const T Db = (T)(g.dsd[k] * (Cb - SW)) - bP * (g.Hkk[k] * xb + ds * SX);
-    SX += g.hk_rds[k] * xb;
-    if (k > 0) SW += (double)a.aW[(size_t)k * plane + n];
+    const T xb = ldg(yPhi + (size_t)k * plane + n);
+    const T ds = ldg(g.ds + k);
+    const T Db = (T)(ldg(g.dsd + k) * (Cb - SW)) - bP * (ldg(g.Hkk + k) * xb + ds * SX);
+    SX += ldg(g.hk_rds + k) * xb;
+    if (k > 0) SW += (double)ldg(a.aW + (size_t)k * plane + n);
     const size_t r3 = (size_t)k * plane + (size_t)j * I;
-    aadd(a.aFl + r3 + fE, Db * g.rdx[j]);
-    aadd(a.aFl + r3 + fW, -Db * g.rdx[j]);
+    aadd(a.aFl + r3 + fE, Db * rdxj);
+    aadd(a.aFl + r3 + fW, -Db * rdxj);
     const size_t rv = ((size_t)k * (J - 1) + j) * I;
-    if (j < J - 1) aadd(a.aFt + rv + i, Db * g.sv[j] * g.rdy[j]);
-    if (j > 0) aadd(a.aFt + rv - I + i, -Db * g.sv[j - 1] * g.rdy[j]);
+    if (j < J - 1) aadd(a.aFt + rv + i, Db * csS);
+    if (j > 0) aadd(a.aFt + rv - I + i, -Db * csN);
   }
 }
 
@@ -393,7 +397,9 @@ __global__ void __launch_bounds__(128) k_adj_column(Geom<T> g, const T* __restri
 template <class T>
 __global__ void __launch_bounds__(128) k_adj_conv(Geom<T> g, const T* __restrict__ U, const T* __restrict__ V,
                                                   const T* __restrict__ Phi, ColState<T> cs, AdjBufs<T> a,
-                                                  T* oU, T* oV, T* oPhi, T scale, int accumulate) {
+                                                  T* oU, T* oV, T* oPhi, T scale, int accumulate, T* sU, T* sV,
+                                                  T* sPhi) {
+  // out = (accumulate ? out : 0) + scale * b; when sU is given, also sum += scale * b
   const int I = g.I, J = g.J, K = g.K;
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= I * J) return;
@@ -402,24 +408,29 @@ __global__ void __launch_bounds__(128) k_adj_conv(Geom<T> g, const T* __restrict
   const bool hasV = j < J - 1;
   const T Puc = cs.Pu[n], rPuc = cs.rPu[n], rPc = cs.rP[n];
   const T Pvc = hasV ? cs.Pv[n] : T(0), rPvc = hasV ? cs.rPv[n] : T(0);
-  T aPu = 0, arPu = 0, aPv = 0, arPv = 0, arP = a.arPcol[n];
+  T aPu = 0, arPu = 0, aPv = 0, arPv = 0, arP = ldg(a.arPcol + n);
   for (int k = 0; k < K; ++k) {
     const size_t o = (size_t)k * plane + n;
-    const T Uk = U[o], Pk = Phi[o];
-    const T bu = a.aU[o] + a.aFl[o] * Puc + a.aGu[o] * rPuc;
-    aPu += a.aFl[o] * Uk + a.tPu[o];
-    arPu += a.aGu[o] * Uk + a.tRPu[o];
-    const T bp = a.aPhi[o] + a.aGs[o] * rPc;
-    arP += a.aGs[o] * Pk + a.tRP[o];
+    const T Uk = ldg(U + o), Pk = ldg(Phi + o);
+    const T bu = ldg(a.aU + o) + ldg(a.aFl + o) * Puc + ldg(a.aGu + o) * rPuc;
+    aPu += ldg(a.aFl + o) * Uk + ldg(a.tPu + o);
+    arPu += ldg(a.aGu + o) * Uk + ldg(a.tRPu + o);
+    const T bp = ldg(a.aPhi + o) + ldg(a.aGs + o) * rPc;
+    arP += ldg(a.aGs + o) * Pk + ldg(a.tRP + o);
     oU[o] = (accumulate ? oU[o] : T(0)) + scale * bu;
     oPhi[o] = (accumulate ? oPhi[o] : T(0)) + scale * bp;
+    if (sU) {
+      sU[o] += scale * bu;
+      sPhi[o] += scale * bp;
+    }
     if (hasV) {
       const size_t ov = (size_t)k * vplane + n;
-      const T Vk = V[ov];
-      const T bv = a.aV[ov] + a.aFt[ov] * Pvc + a.aGv[ov] * rPvc;
-      aPv += a.aFt[ov] * Vk + a.tPv[ov];
-      arPv += a.aGv[ov] * Vk + a.tRPv[ov];
+      const T Vk = ldg(V + ov);
+      const T bv = ldg(a.aV + ov) + ldg(a.aFt + ov) * Pvc + ldg(a.aGv + ov) * rPvc;
+      aPv += ldg(a.aFt + ov) * Vk + ldg(a.tPv + ov);
+      arPv += ldg(a.aGv + ov) * Vk + ldg(a.tRPv + ov);
       oV[ov] = (accumulate ? oV[ov] : T(0)) + scale * bv;
+      if (sU) sV[ov] += scale * bv;
     }
   }
   // P^u = sqrt(m^u): dP^u/dm^u = 1/(2 P^u), d(1/P^u)/dm^u = -1/(2 P^u^3)
@@ -431,7 +442,8 @@ __global__ void __launch_bounds__(128) k_adj_conv(Geom<T> g, const T* __restrict
 // pi-bar = direct psi part + m-bar, with m^u_i = (m_i + m_{i+1})/2 and
 // m^v_j = (m_j + m_{j+1})/2 transposed as gathers.
 template <class T>
-__global__ void __launch_bounds__(256) k_adj_colstate(Geom<T> g, AdjBufs<T> a, T* opi, T scale, int accumulate) {
+__global__ void __launch_bounds__(256) k_adj_colstate(Geom<T> g, AdjBufs<T> a, T* opi, T scale, int accumulate,
+                                                      T* spi) {
   const int I = g.I, J = g.J;
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= I * J) return;
@@ -441,13 +453,7 @@ __global__ void __launch_bounds__(256) k_adj_colstate(Geom<T> g, AdjBufs<T> a, T
   if (j > 0) mb += T(0.5) * a.mvb[n - I];
   const T v = a.aPiD[n] + mb;
   opi[n] = (accumulate ? opi[n] : T(0)) + scale * v;
-}
-
-// y += s * x over n elements (adjoint accumulation between stages)
-template <class T>
-__global__ void __launch_bounds__(256) k_axpy(size_t n, T s, const T* __restrict__ x, T* y) {
-  const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q < n) y[q] += s * x[q];
+  if (spi) spi[n] += scale * v;
 }
 
 }  // namespace agcm

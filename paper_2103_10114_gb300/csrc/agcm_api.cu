@@ -128,14 +128,13 @@ enum KernelId : int {
   KID_ADJ_UPDATE,
   KID_ADJ_COLUMN,
   KID_ADJ_COLSTATE,
-  KID_ADJ_AXPY,
   KID_ENSEMBLE,
   KID_FILTER,
   KID_COUNT
 };
 static const char* const kKernelNames[KID_COUNT] = {
     "k_colstate", "k_column", "k_update", "k_fused_colsum", "k_fused_stage", "k_diag",
-    "k_adj_update", "k_adj_column", "k_adj_colstate", "k_adj_axpy", "k_ensemble", "k_filter"};
+    "k_adj_update", "k_adj_column", "k_adj_colstate", "k_ensemble", "k_filter"};
 
 struct Profiler {
   bool on = false;
@@ -1025,10 +1024,11 @@ int ensure_adj(agcm_state* s) {
   return AGCM_OK;
 }
 
-// out = (accumulate ? out : 0) + scale * J(x)^T y, J the Jacobian of T at x.
+// out = (accumulate ? out : 0) + scale * J(x)^T y, J the Jacobian of T at x;
+// with sum != nullptr also sum += scale * J(x)^T y.
 template <class T>
 int vjp(agcm_state* s, void* const x[4], const void* const y[4], void* const out[4], double scale, int accumulate,
-        cudaStream_t st) {
+        cudaStream_t st, void* const* sum = nullptr) {
   const agcm::Geom<T>& G = geom_of<T>(s);
   const size_t n2 = s->n2, n3 = s->n3, nv = s->nv, e = s->esz;
   agcm::ColState<T> cs{(T*)s->col[0], (T*)s->col[1], (T*)s->col[2], (T*)s->col[3], (T*)s->col[4], (T*)s->col[5]};
@@ -1066,19 +1066,11 @@ int vjp(agcm_state* s, void* const x[4], const void* const y[4], void* const out
   s->prof.end(st);
   s->prof.begin(KID_ADJ_COLSTATE, st);
   agcm::k_adj_conv<T><<<nblocks(n2, 128), 128, 0, st>>>(G, (const T*)x[0], (const T*)x[1], (const T*)x[2], cs, a,
-                                                        (T*)out[0], (T*)out[1], (T*)out[2], (T)scale, accumulate);
-  agcm::k_adj_colstate<T><<<nblocks(n2, 256), 256, 0, st>>>(G, a, (T*)out[3], (T)scale, accumulate);
-  s->prof.end(st);
-  CUDA_TRY(cudaGetLastError());
-  return AGCM_OK;
-}
-
-template <class T>
-int axpy4(agcm_state* s, const void* const x[4], void* const y[4], cudaStream_t st) {
-  const size_t n[4] = {s->n3, s->nv, s->n3, s->n2};
-  s->prof.begin(KID_ADJ_AXPY, st);
-  for (int f = 0; f < 4; ++f)
-    if (n[f]) agcm::k_axpy<T><<<nblocks(n[f], 256), 256, 0, st>>>(n[f], T(1), (const T*)x[f], (T*)y[f]);
+                                                        (T*)out[0], (T*)out[1], (T*)out[2], (T)scale, accumulate,
+                                                        sum ? (T*)sum[0] : nullptr, sum ? (T*)sum[1] : nullptr,
+                                                        sum ? (T*)sum[2] : nullptr);
+  agcm::k_adj_colstate<T><<<nblocks(n2, 256), 256, 0, st>>>(G, a, (T*)out[3], (T)scale, accumulate,
+                                                            sum ? (T*)sum[3] : nullptr);
   s->prof.end(st);
   CUDA_TRY(cudaGetLastError());
   return AGCM_OK;
@@ -1099,10 +1091,9 @@ int adjoint_step(agcm_state* s, const void* const lam_in[4], void* const lam_out
     if (n[f]) CUDA_TRY(cudaMemcpyAsync(lam_out[f], lam_in[f], n[f] * s->esz, cudaMemcpyDeviceToDevice, st));
   void* const* mu2 = s->mu[0];
   void* const* mu1 = s->mu[1];
-  if ((rc = vjp<T>(s, s->x[2], lam_in, mu2, dt, 0, st))) return rc;
-  if ((rc = axpy4<T>(s, mu2, lam_out, st))) return rc;
-  if ((rc = vjp<T>(s, s->x[1], mu2, mu1, 0.5 * dt, 0, st))) return rc;
-  if ((rc = axpy4<T>(s, mu1, lam_out, st))) return rc;
+  // each product also adds itself to lam_out (no separate accumulation pass)
+  if ((rc = vjp<T>(s, s->x[2], lam_in, mu2, dt, 0, st, lam_out))) return rc;
+  if ((rc = vjp<T>(s, s->x[1], mu2, mu1, 0.5 * dt, 0, st, lam_out))) return rc;
   return vjp<T>(s, s->x[0], mu1, lam_out, 0.5 * dt, 1, st);
 }
 

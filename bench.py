@@ -270,7 +270,7 @@ def main():
     # dominant kernel and its algorithmic bytes (one stage: 6/9/9 words per point -> 8 on average)
     name, (kms, kn) = max(prof.items(), key=lambda kv: kv[1][0])
     stage_bytes = pts * 8 * esz
-    achieved = stage_bytes / (kms / kn / 1e3) / 1e9 if name in ("k_update", "k_fused_stage") else None
+    achieved = stage_bytes / (kms / kn / 1e3) / 1e9 if name == "k_fused_stage" else None
     traffic, traffic_src = None, None
     rec = NCU_TRAFFIC.get(name)
     if rec and rec[0] == kernel_source_hash():

@@ -121,8 +121,7 @@ struct agcm_grid {
 enum KernelId : int {
   KID_COLSTATE = 0,
   KID_COLUMN,
-  KID_UPDATE,
-  KID_FUSED_PRE,
+  KID_VSUM,
   KID_FUSED,
   KID_DIAG,
   KID_ADJ_UPDATE,
@@ -133,7 +132,7 @@ enum KernelId : int {
   KID_COUNT
 };
 static const char* const kKernelNames[KID_COUNT] = {
-    "k_colstate", "k_column", "k_update", "k_fused_colsum", "k_fused_stage", "k_diag",
+    "k_colstate", "k_column", "k_vsum", "k_fused_stage", "k_diag",
     "k_adj_update", "k_adj_column", "k_adj_colstate", "k_ensemble", "k_filter"};
 
 struct Profiler {
@@ -367,31 +366,6 @@ inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s
 
 inline unsigned nblocks(size_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
-// ------------------------------------------------------------- stage driver
-// One stage: out = base + cdt * T(xs).  base == nullptr gives T(xs) itself.
-template <class T>
-int run_stage(agcm_state* s, const agcm::Geom<T>& G, void* const xs[4], void* const base[4],
-              void* const out[4], double cdt, cudaStream_t st) {
-  const size_t n2 = s->n2, n3 = s->n3;
-  agcm::ColState<T> cs{(T*)s->col[0], (T*)s->col[1], (T*)s->col[2], (T*)s->col[3], (T*)s->col[4], (T*)s->col[5]};
-  s->prof.begin(KID_COLSTATE, st);
-  agcm::k_colstate<T><<<nblocks(n2, 256), 256, 0, st>>>(G, (const T*)xs[3], cs);
-  s->prof.end(st);
-  s->prof.begin(KID_COLUMN, st);
-  agcm::k_column<T><<<nblocks(n2, 128), 128, 0, st>>>(G, (const T*)xs[0], (const T*)xs[1], (const T*)xs[2],
-                                                      (const T*)xs[3], cs, (T*)s->W, (T*)s->X, (T*)s->psi,
-                                                      (const T*)base[3], (T*)out[3], cdt, s->C);
-  s->prof.end(st);
-  s->prof.begin(KID_UPDATE, st);
-  agcm::k_update<T><<<nblocks(n3, 256), 256, 0, st>>>(G, (const T*)xs[0], (const T*)xs[1], (const T*)xs[2], cs,
-                                                      (const T*)s->W, (const T*)s->X, (const T*)s->psi,
-                                                      (const T*)base[0], (const T*)base[1], (const T*)base[2],
-                                                      (T*)out[0], (T*)out[1], (T*)out[2], (T)cdt);
-  s->prof.end(st);
-  CUDA_TRY(cudaGetLastError());
-  return AGCM_OK;
-}
-
 template <class T>
 const agcm::Geom<T>& geom_of(const agcm_state* s) {
   if constexpr (sizeof(T) == 8)
@@ -405,7 +379,7 @@ template <class T>
 int ensure_bar(agcm_state* s, cudaStream_t st) {
   if (s->bar_valid) return AGCM_OK;
   const agcm::Geom<T>& G = geom_of<T>(s);
-  s->prof.begin(KID_FUSED_PRE, st);
+  s->prof.begin(KID_VSUM, st);
   agcm::k_vsum<T><<<nblocks(s->n2, 256), 256, 0, st>>>(G, (const T*)s->x[0][0], (const T*)s->x[0][1], s->ubar[0],
                                                        s->vbar[0]);
   s->prof.end(st);

@@ -1,0 +1,96 @@
+"""The C ABI's contract on the GPU: states on different streams do not
+interfere (the library keeps no hidden mutable state between them), argument
+errors are refused with AGCM_EINVAL and leave the state usable, and the
+per-kernel profiler counts what ran."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2103_10114_gb300 import agcm, inputs
+
+pytestmark = pytest.mark.gpu
+FIELDS = agcm.FIELDS
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built(cuda_ok):
+    agcm.build()
+    agcm.lib()
+
+
+def to_np(d):
+    return {f: v.double().cpu().numpy() for f, v in d.items()}
+
+
+@pytest.mark.parametrize("prec", [agcm.AGCM_FP32, agcm.AGCM_FP64])
+def test_concurrent_states_on_streams_match_sequential(prec):
+    import torch
+
+    cases = [(128, 64, 8, 3), (96, 48, 6, 4), (128, 64, 8, 5)]  # two share a grid shape
+    grids, states, ref = [], [], []
+    for I, J, K, seed in cases:
+        st = inputs.baroclinic_jet(I, J, K, seed=seed, noise=1e-2, terrain_seed=2)
+        g = agcm.Grid(I, J, K, phis=st["phis"])
+        dt = g.dt(100.0)
+        s = agcm.State(g, prec)
+        s.load(st)
+        for _ in range(4):  # one call per step, as below (FP32 refreshes its column means per call)
+            s.step(1, dt)
+        ref.append(to_np(s.store()))
+        s.load(st)  # back to the initial state
+        grids.append((g, dt))
+        states.append(s)
+    torch.cuda.synchronize()
+    streams = [torch.cuda.Stream() for _ in states]
+    for _ in range(4):  # interleave single steps on three streams
+        for (g, dt), s, q in zip(grids, states, streams):
+            s.step(1, dt, stream=q)
+    torch.cuda.synchronize()
+    for s, r in zip(states, ref):
+        out = to_np(s.store())
+        for f in FIELDS:
+            assert np.array_equal(out[f], r[f]), f
+        s.close()
+
+
+def test_argument_errors_leave_the_state_usable():
+    I, J, K = 64, 32, 6
+    st = inputs.rossby_haurwitz4(I, J, K, seed=1)
+    g = agcm.Grid(I, J, K, phis=st["phis"])
+    s = agcm.State(g, agcm.AGCM_FP32)
+    s.load(st)
+    L = agcm.lib()
+    stream = ctypes.c_void_p(0)
+    assert L.agcm_step(s.handle, -1, 10.0, stream) == agcm.AGCM_EINVAL
+    assert L.agcm_step(s.handle, 1, float("nan"), stream) == agcm.AGCM_EINVAL
+    assert L.agcm_step(s.handle, 1, float("inf"), stream) == agcm.AGCM_EINVAL
+    assert L.agcm_step_split(s.handle, 1, 10.0, 0, stream) == agcm.AGCM_EINVAL
+    assert L.agcm_filter(s.handle, 0.5, stream) == agcm.AGCM_EINVAL
+    assert L.agcm_step(s.handle, 0, 10.0, stream) == agcm.AGCM_OK  # nothing to do
+    # the grid cannot go while a state uses it
+    assert L.agcm_grid_destroy(g.handle) == agcm.AGCM_EINVAL
+    before = to_np(s.store())
+    s.step(1, g.dt(100.0))
+    after = to_np(s.store())
+    assert all(np.isfinite(after[f]).all() for f in FIELDS)
+    assert any(not np.array_equal(after[f], before[f]) for f in FIELDS)
+    s.close()
+
+
+def test_profiler_counts_launches():
+    I, J, K = 64, 32, 6
+    st = inputs.rossby_haurwitz4(I, J, K, seed=1)
+    g = agcm.Grid(I, J, K, phis=st["phis"])
+    s = agcm.State(g, agcm.AGCM_FP32)
+    s.load(st)
+    s.profile(True)
+    s.step(5, g.dt(100.0))
+    s.filter()
+    prof = s.profile_read()
+    s.profile(False)
+    assert prof["k_fused_stage"][1] == 15  # three stages per step
+    assert prof["k_vsum"][1] == 1  # exact vertical means once per step call after a load
+    assert prof["k_filter"][1] == 1
+    assert all(ms > 0 for ms, n in prof.values())
+    s.close()

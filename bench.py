@@ -566,7 +566,7 @@ def measure_ensemble(agcm, inputs, torch, steps=10, per_member=True):
     ens.profile(False)
     ens.status()
     res = {"value": pts / (ms / 1e3), "unit": "gp-steps/s", "ms_per_step": ms, "points": pts,
-           "shape": list(shape), "tuned_ms": {f"{w}x{b}": round(t, 4) for (w, b), t in times.items()},
+           "shape": list(shape), "tuned_ms": {"x".join(map(str, k)): round(t, 4) for k, t in times.items()},
            "hbm_frac_step": pts / (ms / 1e3) * 96 / (peaks()[0] * 1e9)}
     ens.close()
     for s in states:

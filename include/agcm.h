@@ -244,7 +244,10 @@ const char* agcm_kernel_name(int id);
  * CUDA graph once a first call has uploaded the dt values (nsteps = 0 only
  * prepares: it uploads dt and the members' vertical means without stepping).
  * agcm_ensemble_configure sets the launch shape (warps per block: 1; blocks
- * per SM, 0 = as many as fit); an autotuner picks it (ensemble.py).
+ * per SM, 0 = as many as fit); agcm_ensemble_tile sets the row tile of a
+ * work item (1, 2 or 4 consecutive rows of 32 columns, taken by one warp in
+ * order); an autotuner picks both (ensemble.py).  Set both before capturing
+ * a graph: a replay keeps the shape it was captured with.
  * agcm_ensemble_set_timeout: barrier timeout in seconds; test_missing_blocks
  * > 0 makes every barrier wait for blocks that do not exist, to exercise the
  * timeout path (tests only).  agcm_ensemble_profile: enable (1) / disable (0)
@@ -255,6 +258,7 @@ typedef struct agcm_ensemble agcm_ensemble_t;
 int agcm_ensemble_create(agcm_state_t* const* members, int n, agcm_ensemble_t** out);
 int agcm_ensemble_destroy(agcm_ensemble_t* ens);
 int agcm_ensemble_configure(agcm_ensemble_t* ens, int warps_per_block, int blocks_per_sm);
+int agcm_ensemble_tile(agcm_ensemble_t* ens, int rows_per_item);
 int agcm_ensemble_set_timeout(agcm_ensemble_t* ens, double seconds, int test_missing_blocks);
 int agcm_ensemble_step(agcm_ensemble_t* ens, int nsteps, const double* dt, void* stream);
 int agcm_ensemble_status(agcm_ensemble_t* ens, void* stream);

@@ -102,6 +102,7 @@ SIGNATURES = {
     "agcm_ensemble_create": (_i, [ctypes.POINTER(_vp), _i, ctypes.POINTER(_vp)]),
     "agcm_ensemble_destroy": (_i, [_vp]),
     "agcm_ensemble_configure": (_i, [_vp, _i, _i]),
+    "agcm_ensemble_tile": (_i, [_vp, _i]),
     "agcm_ensemble_set_timeout": (_i, [_vp, _d, _i]),
     "agcm_ensemble_step": (_i, [_vp, _i, _pd, _vp]),
     "agcm_ensemble_status": (_i, [_vp, _vp]),

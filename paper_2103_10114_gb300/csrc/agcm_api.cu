@@ -1265,6 +1265,7 @@ struct agcm_ensemble {
   int nitems = 0;
   int warps_per_block = 1;
   int blocks_per_sm = 0;         // 0: as many as fit
+  int rows_per_item = 1;         // row tile of a work item
   double timeout_s = 1.0;
   int test_missing = 0;
   bool desc_dirty = true;
@@ -1290,7 +1291,7 @@ void fill_desc(agcm_ensemble* e) {
     d[m].nbx = (s->grid->I + 31) / 32;
     d[m].item_begin = begin;
     d[m].dt = (T)0;
-    begin += d[m].nbx * s->grid->J;
+    begin += d[m].nbx * ((s->grid->J + e->rows_per_item - 1) / e->rows_per_item);
   }
   e->nitems = begin;
 }
@@ -1319,7 +1320,9 @@ int ensemble_step(agcm_ensemble* e, int nsteps, const double* dt, cudaStream_t s
   CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   CUDA_TRY(cudaDeviceGetAttribute(&clock_khz, cudaDevAttrClockRate, dev));
   const int threads = 32 * e->warps_per_block;
-  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, agcm::k_ensemble<T>, threads, 0));
+  auto kern = e->rows_per_item == 4 ? agcm::k_ensemble<T, 4>
+                                    : (e->rows_per_item == 2 ? agcm::k_ensemble<T, 2> : agcm::k_ensemble<T, 1>);
+  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, 0));
   if (occ < 1) return fail(AGCM_EINVAL, "ensemble kernel does not fit with %d threads per block", threads);
   const int per_sm = e->blocks_per_sm > 0 ? std::min(e->blocks_per_sm, occ) : occ;
   const unsigned grid = (unsigned)(per_sm * nsm);
@@ -1329,8 +1332,8 @@ int ensemble_step(agcm_ensemble* e, int nsteps, const double* dt, cudaStream_t s
     const int chunk = std::min(e->queue_cap, nsteps - done);
     CUDA_TRY(cudaMemsetAsync(e->d_sync, 0, sync_bytes, st));
     e->prof.begin(KID_ENSEMBLE, st);
-    agcm::k_ensemble<T><<<grid, threads, 0, st>>>((const agcm::EnsMember<T>*)e->d_desc, (int)n, e->nitems, chunk,
-                                                  e->d_sync, grid + (unsigned)e->test_missing, limit);
+    kern<<<grid, threads, 0, st>>>((const agcm::EnsMember<T>*)e->d_desc, (int)n, e->nitems, chunk, e->d_sync,
+                                   grid + (unsigned)e->test_missing, limit);
     e->prof.end(st);
     CUDA_TRY(cudaGetLastError());
   }
@@ -1396,6 +1399,31 @@ int agcm_ensemble_configure(agcm_ensemble_t* e, int warps_per_block, int blocks_
     return fail(AGCM_EINVAL, "warps_per_block must be 1 and blocks_per_sm >= 0");
   e->warps_per_block = warps_per_block;
   e->blocks_per_sm = blocks_per_sm;
+  return AGCM_OK;
+}
+
+int agcm_ensemble_tile(agcm_ensemble_t* e, int rows_per_item) {
+  if (!e || (rows_per_item != 1 && rows_per_item != 2 && rows_per_item != 4))
+    return fail(AGCM_EINVAL, "rows_per_item must be 1, 2 or 4");
+  if (rows_per_item == e->rows_per_item) return AGCM_OK;
+  e->rows_per_item = rows_per_item;
+  // item ranges change; the descriptor (with its dt) is uploaded again at the next step
+  const std::vector<char> old = e->host_desc;
+  if (e->prec == AGCM_FP64)
+    fill_desc<double>(e);
+  else
+    fill_desc<float>(e);
+  const size_t n = e->members.size();
+  if (e->prec == AGCM_FP64) {
+    for (size_t m = 0; m < n; ++m)
+      reinterpret_cast<agcm::EnsMember<double>*>(e->host_desc.data())[m].dt =
+          reinterpret_cast<const agcm::EnsMember<double>*>(old.data())[m].dt;
+  } else {
+    for (size_t m = 0; m < n; ++m)
+      reinterpret_cast<agcm::EnsMember<float>*>(e->host_desc.data())[m].dt =
+          reinterpret_cast<const agcm::EnsMember<float>*>(old.data())[m].dt;
+  }
+  e->desc_dirty = true;
   return AGCM_OK;
 }
 

@@ -1,7 +1,9 @@
 // agcm_ensemble.cuh — many members of uneven resolution in one persistent launch.
 //
-// Each member is a state on its own grid.  A work item is one row segment of
-// 32 columns of one member; each warp pulls items from a per-(step, stage)
+// Each member is a state on its own grid.  A work item is a row tile of one
+// member: 32 columns of `rows` consecutive rows (the warp takes the rows one
+// after the other, so a row's stencil rows are still in L1 for the next); each
+// warp pulls items from a per-(step, stage)
 // device counter and runs the same column body as the single-state stage
 // kernel (fused_column), so a member advanced in an ensemble does the same
 // arithmetic as alone; the two kernels are compiled separately, so the
@@ -24,7 +26,7 @@ struct EnsMember {
   double* vbar[3];
   T dt;
   int nbx;            // 32-column blocks per row
-  int item_begin;     // first global item of this member
+  int item_begin;     // first global item of this member (nbx * ceil(J / rows) items)
 };
 
 struct EnsSync {
@@ -85,7 +87,9 @@ __device__ __forceinline__ int ens_member_of(const EnsMember<T>* mem, int nmem, 
 #ifndef AGCM_ENS_MINB
 #define AGCM_ENS_MINB 12
 #endif
-template <class T>
+// ROWS: the row tile of a work item (a compile-time count, so that the
+// one-row kernel carries no row loop).
+template <class T, int ROWS>
 __global__ void __launch_bounds__(32, sizeof(T) == 4 ? AGCM_ENS_MINB : 8)
     k_ensemble(const EnsMember<T>* __restrict__ mem, int nmem, int nitems, int nsteps, EnsSync* sy,
                unsigned expected_blocks, long long limit) {
@@ -112,18 +116,23 @@ __global__ void __launch_bounds__(32, sizeof(T) == 4 ? AGCM_ENS_MINB : 8)
           cur = m;
         }
         const int local = item - e.item_begin;
-        const int j = local / e.nbx;
-        const int i = (local - j * e.nbx) * 32 + lane;
-        if (i < e.g.I) {
-          const Geom<T>& g = e.g;
-          // stage 1: x_n -> x1 (dt/2); stage 2: x1 -> x2 (dt/2); stage 3: x2 -> x_n
-          // in place (dt); the base is x_n in all three (stage 1 reads it
-          // as base instead of reusing its own values: the same arithmetic)
-          const int a = stage, b = stage == 0 ? 1 : (stage == 1 ? 2 : 0);
-          const T c = stage == 2 ? e.dt : T(0.5) * e.dt;
-          fused_column<T, 2, false>(g, i, j, e.x[a][0], e.x[a][1], e.x[a][2], e.x[a][3], e.ubar[a], e.vbar[a],
-                                    e.x[0][0], e.x[0][1], e.x[0][2], e.x[0][3], e.x[b][0], e.x[b][1], e.x[b][2],
-                                    e.x[b][3], e.ubar[b], e.vbar[b], e.ubar[0], e.vbar[0], c);
+        const int jt = local / e.nbx;
+        const int i = (local - jt * e.nbx) * 32 + lane;
+#pragma unroll 1
+        for (int r = 0; r < ROWS; ++r) {
+          const int j = jt * ROWS + r;
+          if (j >= e.g.J) break;  // warp-uniform
+          if (i < e.g.I) {
+            const Geom<T>& g = e.g;
+            // stage 1: x_n -> x1 (dt/2); stage 2: x1 -> x2 (dt/2); stage 3: x2 -> x_n
+            // in place (dt); the base is x_n in all three (stage 1 reads it
+            // as base instead of reusing its own values: the same arithmetic)
+            const int a = stage, b = stage == 0 ? 1 : (stage == 1 ? 2 : 0);
+            const T c = stage == 2 ? e.dt : T(0.5) * e.dt;
+            fused_column<T, 2, false>(g, i, j, e.x[a][0], e.x[a][1], e.x[a][2], e.x[a][3], e.ubar[a], e.vbar[a],
+                                      e.x[0][0], e.x[0][1], e.x[0][2], e.x[0][3], e.x[b][0], e.x[b][1],
+                                      e.x[b][2], e.x[b][3], e.ubar[b], e.vbar[b], e.ubar[0], e.vbar[0], c);
+          }
         }
       }
       __threadfence();

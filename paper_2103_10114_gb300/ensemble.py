@@ -1,12 +1,13 @@
 """Ensembles of members of uneven resolution: one persistent launch per call,
 an autotuner for its launch shape, and CUDA-graph replay.
 
-The launch shape (one-warp blocks, how many resident per SM) decides how the
-work items (32-column row segments of every member) are spread over the SMs
-and how many warps hide each other's memory latency; the best
-shape depends on the member mix and the GPU, so `autotune` times each
-candidate on the ensemble itself and keeps the fastest (cached per member mix
-and device name for the life of the process).
+The launch shape (one-warp blocks, how many resident per SM) and the row tile
+of a work item (32 columns of 1, 2 or 4 consecutive rows, taken in order by one
+warp) decide how the work is spread over the SMs, how many warps hide each
+other's memory latency and how much of a row's stencil is still in L1 for the
+next row; the best choice depends on the member mix and the GPU, so
+`autotune` times each candidate on the ensemble itself and keeps the fastest
+(cached per member mix and device name for the life of the process).
 """
 from __future__ import annotations
 
@@ -24,7 +25,7 @@ class Ensemble:
         h = ctypes.c_void_p()
         agcm.check(agcm.lib().agcm_ensemble_create(arr, len(self.states), ctypes.byref(h)))
         self._h = h
-        self.shape = (1, 0)
+        self.shape = (1, 0, 1)
 
     @property
     def handle(self):
@@ -33,9 +34,11 @@ class Ensemble:
     def points(self):
         return sum(s.grid.points() for s in self.states)
 
-    def configure(self, warps_per_block, blocks_per_sm):
+    def configure(self, warps_per_block, blocks_per_sm, rows_per_item=1):
+        """Launch shape and row tile: (warps per block, blocks per SM, rows per item)."""
         agcm.check(agcm.lib().agcm_ensemble_configure(self._h, int(warps_per_block), int(blocks_per_sm)))
-        self.shape = (int(warps_per_block), int(blocks_per_sm))
+        agcm.check(agcm.lib().agcm_ensemble_tile(self._h, int(rows_per_item)))
+        self.shape = (int(warps_per_block), int(blocks_per_sm), int(rows_per_item))
 
     def set_timeout(self, seconds, test_missing_blocks=0):
         agcm.check(agcm.lib().agcm_ensemble_set_timeout(self._h, float(seconds), int(test_missing_blocks)))
@@ -72,7 +75,7 @@ class Ensemble:
             self.configure(*_TUNE_CACHE[key])
             return _TUNE_CACHE[key], {}
         if candidates is None:
-            candidates = [(1, b) for b in (0, 8, 12, 16, 20, 24)]
+            candidates = [(1, b, r) for r in (1, 2, 4) for b in (0, 8, 16)]
         saved = [s.store() for s in self.states]
         times = {}
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -33,10 +33,14 @@ def np_state(s):
     return {f: v.double().cpu().numpy() for f, v in s.store().items()}
 
 
-@pytest.mark.parametrize("prec", [agcm.AGCM_FP32, agcm.AGCM_FP64])
-def test_member_equals_single_run(prec):
+@pytest.mark.parametrize("prec,rows", [(agcm.AGCM_FP32, 1), (agcm.AGCM_FP64, 1), (agcm.AGCM_FP32, 2),
+                                       (agcm.AGCM_FP64, 4)])
+def test_member_equals_single_run(prec, rows):
+    """Every member after three ensemble steps equals its own run; row tiles
+    of 2 and 4 rows leave ragged last tiles on the member grids (nlat 23)."""
     mem = members(prec)
     ens = Ensemble([m[1] for m in mem])
+    ens.configure(1, 0, rows)
     dts = [m[3] for m in mem]
     ens.step(3, dts)
     ens.status()

@@ -1,19 +1,22 @@
 // agcm_api.cu — implementation of the C ABI declared in include/agcm.h.
 //
-// Host side: grid geometry (Eq. 7 leap strides, metric terms, sigma tables),
-// the CFL time step, device memory, the three-stage step driver and the
-// diagnostics.  Device side: the kernels in agcm_phases.cuh / agcm_fused.cuh /
-// agcm_adjoint.cuh / agcm_diag.cuh.
+// Host side: grid geometry (Eq. 7 leap strides, metric terms, sigma tables,
+// the standard stratification), the CFL time step, device memory, the
+// three-stage step driver (unsplit and split), the low-latitude filters, the
+// adjoint driver, the diagnostics, ensembles and the allocation-free
+// tendency.  Device side: the kernels in agcm_fused.cuh (the stage),
+// agcm_phases.cuh / agcm_adjoint.cuh (the adjoint), agcm_diag.cuh,
+// agcm_ensemble.cuh and agcm_filter.cuh.
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <type_traits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/agcm.h"
@@ -189,12 +192,12 @@ struct agcm_state {
   size_t n3 = 0, nv = 0, n2 = 0;
   // prognostic x_n and the stage states x1, x2 (U, V, Phi, pi packed)
   void* x[3][4] = {};
-  // phase scratch: P, rP, Pu, rPu, Pv, rPv (2-D), W ((K+1) planes), X, psi, C (FP64)
+  // adjoint forward-recompute scratch (allocated with the adjoint workspace):
+  // P, rP, Pu, rPu, Pv, rPv (2-D), W ((K+1) planes), X, psi
   void* col[6] = {};
   void* W = nullptr;
   void* X = nullptr;
   void* psi = nullptr;
-  double* C = nullptr;
   // FP64 vertical means sum_k dsigma U_k and V_k of x[0..2] (J*I each), the
   // input of the fused stage kernel's column integral; bar_valid for x[0]
   double* ubar[3] = {};
@@ -765,11 +768,6 @@ int agcm_state_create(const agcm_grid_t* g, int precision, int nmembers, agcm_st
     ok = ok && (s->x[c][2] = get(s->n3 * s->esz));
     ok = ok && (s->x[c][3] = get(s->n2 * s->esz));
   }
-  for (int c = 0; c < 6 && ok; ++c) ok = ok && (s->col[c] = get(s->n2 * s->esz));
-  ok = ok && (s->W = get((K + 1) * J * I * s->esz));
-  ok = ok && (s->X = get(s->n3 * s->esz));
-  ok = ok && (s->psi = get(s->n3 * s->esz));
-  ok = ok && (s->C = (double*)get(s->n2 * sizeof(double)));
   for (int c = 0; c < 3 && ok; ++c) {
     ok = ok && (s->ubar[c] = (double*)get(s->n2 * sizeof(double)));
     ok = ok && (s->vbar[c] = (double*)get(s->n2 * sizeof(double)));
@@ -983,6 +981,11 @@ int ensure_adj(agcm_state* s) {
     else ok = false;
     return p;
   };
+  // forward recompute (phases A, B) at the stage states
+  for (auto& p : s->col) p = get(n2);
+  s->W = get(nw);
+  s->X = get(n3);
+  s->psi = get(n3);
   for (auto& p : s->adj3) p = get(n3);
   for (auto& p : s->adjv) p = get(nv);
   s->adjW = get(nw);

@@ -4,7 +4,7 @@ Tolerances (reading R11, normwise per field, max|gpu - orc| / max|orc|):
   FP64: 1e-12 for one tendency or one step (rounding-order differences only;
         the column sums run as scans on the GPU and as plain sums in the oracle);
         1e-10 after 20 steps (round-off growth of a nonlinear flow).
-  FP32 with FP64 column sums: 1e-5 after one step (spec target).
+  FP32 with FP64 column sums: 1e-5 after one step (the stated precision target).
 """
 import numpy as np
 import pytest

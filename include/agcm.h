@@ -72,7 +72,8 @@ int agcm_set_allocator(agcm_alloc_fn alloc, agcm_free_fn free_fn, void* ctx);
  * agcm_grid_create — the geometry of one grid (host only; no device work).
  * Eq. 6 (leap-format centred difference) and Eq. 7 (N_leap from the
  * 45-degree reference spacing) define the stride tables.
- *   nlon >= 3, nlat >= 2, nlev >= 1.
+ *   nlon >= 3, nlat >= 2, nlev >= 1; nlon*nlat <= 2^30, nlat <= 65535 and
+ *   nlon*nlat*nlev <= 4e9.
  *   sigma_half: nlev+1 half levels, sigma_half[0] = 0, sigma_half[nlev] = 1,
  *               strictly increasing; NULL = uniform.
  *   leap_u:     nlat strides for the scalar/U rows; NULL = Eq. 7 raised to

@@ -609,6 +609,9 @@ int agcm_grid_create(int nlon, int nlat, int nlev, const double* sigma_half, con
     return fail(AGCM_EINVAL, "need nlon >= 3, nlat >= 2, nlev >= 1 (got %d, %d, %d)", nlon, nlat, nlev);
   if ((double)nlon * nlat * nlev > 4.0e9)
     return fail(AGCM_EINVAL, "grid of %d x %d x %d points is too large", nlon, nlat, nlev);
+  // column indices are 32-bit and the stage launch has one grid row per latitude
+  if ((double)nlon * nlat > 1073741824.0 || nlat > 65535)
+    return fail(AGCM_EINVAL, "nlon * nlat must be at most 2^30 and nlat at most 65535 (got %d x %d)", nlon, nlat);
   agcm_grid* g = new agcm_grid;
   const int I = nlon, J = nlat, K = nlev;
   g->I = I; g->J = J; g->K = K;

@@ -59,6 +59,9 @@ def test_grid_validation(L):
         dict(nlon=16, nlat=8, nlev=2, sigma_half=[0.0, 0.7, 0.6]),
         dict(nlon=16, nlat=8, nlev=2, sigma_half=[0.1, 0.5, 1.0]),
         dict(nlon=16, nlat=8, nlev=2, phis=np.full(128, np.nan)),
+        dict(nlon=65536, nlat=32768, nlev=1),  # more columns than 32-bit column indices allow
+        dict(nlon=16, nlat=70000, nlev=1),     # more rows than one launch row per latitude allows
+        dict(nlon=4000, nlat=2000, nlev=600),  # more than 4e9 points
     ]
     for kw in bad:
         with pytest.raises(agcm.AgcmError) as e:

@@ -49,6 +49,11 @@ int fail(int code, const char* fmt, ...) {
     if (e_ != cudaSuccess) return fail(AGCM_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
   } while (0)
 
+// Guards every grid's lazily built device tables and its count of live
+// states and ensembles, so that states may be created and destroyed from
+// several host threads.
+std::mutex g_grid_mu;
+
 // ---------------------------------------------------------------- allocator
 agcm_alloc_fn g_alloc = nullptr;
 agcm_free_fn g_free = nullptr;
@@ -355,6 +360,7 @@ int upload_geom(agcm_grid* g, int p) {
 
 int ensure_geom(const agcm_grid* cg, int prec) {
   agcm_grid* g = const_cast<agcm_grid*>(cg);
+  std::lock_guard<std::mutex> lk(g_grid_mu);
   int dev = 0;
   CUDA_TRY(cudaGetDevice(&dev));
   if (g->dev[prec].ready) {
@@ -587,6 +593,7 @@ static void thermo_tables(agcm_grid* g) {
 
 int agcm_grid_set_thermo(agcm_grid_t* g, const agcm_thermo_t* t) {
   if (!g) return fail(AGCM_EINVAL, "null grid");
+  std::lock_guard<std::mutex> lk(g_grid_mu);
   if (g->dev[0].blob || g->dev[1].blob || g->refs > 0)
     return fail(AGCM_EINVAL, "agcm_grid_set_thermo: the grid already has device tables (call it before the first state)");
   agcm_thermo_t v{0, kT0, 288.15, 6.5e-3, 216.65, 0.0, 0.0, 0.0};
@@ -678,6 +685,7 @@ int agcm_grid_create(int nlon, int nlat, int nlev, const double* sigma_half, con
 
 int agcm_grid_destroy(agcm_grid_t* g) {
   if (!g) return AGCM_OK;
+  std::lock_guard<std::mutex> lk(g_grid_mu);
   if (g->refs > 0) return fail(AGCM_EINVAL, "grid still has %d live states", g->refs);
   for (auto& d : g->dev)
     if (d.blob) dev_free(d.blob);
@@ -793,7 +801,10 @@ int agcm_state_create(const agcm_grid_t* g, int precision, int nmembers, agcm_st
     delete s;
     return fail(AGCM_ECUDA, "state initialisation failed: %s", cudaGetErrorString(cudaGetLastError()));
   }
-  const_cast<agcm_grid*>(g)->refs++;
+  {
+    std::lock_guard<std::mutex> lk(g_grid_mu);
+    const_cast<agcm_grid*>(g)->refs++;
+  }
   *out = s;
   return AGCM_OK;
 }
@@ -802,7 +813,10 @@ int agcm_state_destroy(agcm_state_t* s) {
   if (!s) return AGCM_OK;
   cudaDeviceSynchronize();
   for (void* p : s->owned) dev_free(p);
-  const_cast<agcm_grid*>(s->grid)->refs--;
+  {
+    std::lock_guard<std::mutex> lk(g_grid_mu);
+    const_cast<agcm_grid*>(s->grid)->refs--;
+  }
   delete s;
   return AGCM_OK;
 }
@@ -1385,7 +1399,10 @@ int agcm_ensemble_create(agcm_state_t* const* members, int n, agcm_ensemble_t** 
     delete e;
     return fail(AGCM_ENOMEM, "device allocation for the ensemble failed");
   }
-  for (agcm_state* s : e->members) const_cast<agcm_grid*>(s->grid)->refs++;
+  {
+    std::lock_guard<std::mutex> lk(g_grid_mu);
+    for (agcm_state* s : e->members) const_cast<agcm_grid*>(s->grid)->refs++;
+  }
   *out = e;
   return AGCM_OK;
 }
@@ -1395,7 +1412,10 @@ int agcm_ensemble_destroy(agcm_ensemble_t* e) {
   cudaDeviceSynchronize();
   dev_free(e->d_desc);
   dev_free(e->d_sync);
-  for (agcm_state* s : e->members) const_cast<agcm_grid*>(s->grid)->refs--;
+  {
+    std::lock_guard<std::mutex> lk(g_grid_mu);
+    for (agcm_state* s : e->members) const_cast<agcm_grid*>(s->grid)->refs--;
+  }
   delete e;
   return AGCM_OK;
 }

@@ -94,3 +94,46 @@ def test_profiler_counts_launches():
     assert prof["k_filter"][1] == 1
     assert all(ms > 0 for ms, n in prof.values())
     s.close()
+
+
+def test_states_created_from_many_threads_share_one_grid():
+    """ctypes releases the interpreter lock in foreign calls, so these threads
+    create states on one fresh grid (whose device tables are built by the
+    first) truly at once; every state then steps to the same result."""
+    import threading
+
+    import torch
+
+    I, J, K = 64, 32, 6
+    st = inputs.rossby_haurwitz4(I, J, K, seed=1)
+    g = agcm.Grid(I, J, K, phis=st["phis"])
+    dt = g.dt(100.0)
+    states, errors = [None] * 8, []
+    barrier = threading.Barrier(8)
+
+    def work(q):
+        try:
+            torch.cuda.set_device(0)
+            barrier.wait()
+            states[q] = agcm.State(g, agcm.AGCM_FP32 if q % 2 else agcm.AGCM_FP64)
+        except Exception as e:  # collected and asserted below
+            errors.append(e)
+
+    threads = [threading.Thread(target=work, args=(q,)) for q in range(8)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    outs = {}
+    for q, s in enumerate(states):
+        s.load(st)
+        s.step(2, dt)
+        outs.setdefault(q % 2, []).append(to_np(s.store()))
+    for group in outs.values():
+        for o in group[1:]:
+            for f in FIELDS:
+                assert np.array_equal(o[f], group[0][f]), f
+    for s in states:
+        s.close()
+    g.close()  # no state holds the grid any more

@@ -473,6 +473,11 @@ def measure_forms(agcm, inputs, torch, steps=5):
         ms = _time(torch, lambda: s2.step(20, g2.dt(100.0)), 1) / 20
         out[f"{tag}_256x128x30"] = {"value": I2 * J2 * K2 / (ms / 1e3), "unit": "gp-steps/s", "ms_per_step": ms,
                                     "note": "state fits in L2"}
+        if prec == agcm.AGCM_FP32:  # the same 20 steps replayed from a CUDA graph
+            graph = s2.capture(20, g2.dt(100.0))
+            graph.replay()
+            gms = _time(torch, graph.replay, 3) / 20
+            out[f"{tag}_256x128x30"]["graph"] = {"value": I2 * J2 * K2 / (gms / 1e3), "ms_per_step": gms}
         s2.close()
     try:
         out["split_1440x720x30"] = measure_split(agcm, inputs, torch)

@@ -293,6 +293,23 @@ class State:
     def step(self, nsteps, dt, stream=None):
         check(lib().agcm_step(self._h, int(nsteps), float(dt), _stream_ptr(stream)))
 
+    def capture(self, nsteps, dt):
+        """A CUDA graph of agcm_step(nsteps, dt) on this state; replay it with
+        graph.replay().  The captured call starts by recomputing the FP64 column
+        means from x_n, so a replay stays valid after any load."""
+        import torch
+
+        self.load(self.store())  # marks the column means stale, so the capture recomputes them
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        q = torch.cuda.Stream()
+        q.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(q):
+            with torch.cuda.graph(g, stream=q):
+                self.step(nsteps, dt, stream=q)
+        torch.cuda.current_stream().wait_stream(q)
+        return g
+
     def filter(self, r=0.25, stream=None):
         check(lib().agcm_filter(self._h, float(r), _stream_ptr(stream)))
 

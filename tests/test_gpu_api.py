@@ -137,3 +137,33 @@ def test_states_created_from_many_threads_share_one_grid():
     for s in states:
         s.close()
     g.close()  # no state holds the grid any more
+
+
+@pytest.mark.parametrize("prec", [agcm.AGCM_FP32, agcm.AGCM_FP64])
+def test_step_graph_replay_equals_eager_calls(prec):
+    I, J, K = 96, 48, 8
+    st = inputs.baroclinic_jet(I, J, K, seed=4, noise=1e-2, terrain_seed=2)
+    g = agcm.Grid(I, J, K, phis=st["phis"])
+    dt = g.dt(100.0)
+    a = agcm.State(g, prec)
+    a.load(st)
+    for _ in range(3):
+        a.step(2, dt)
+    want = to_np(a.store())
+    b = agcm.State(g, prec)
+    b.load(st)
+    graph = b.capture(2, dt)
+    for _ in range(3):
+        graph.replay()
+    import torch
+
+    torch.cuda.synchronize()
+    got = to_np(b.store())
+    # FP32 recomputes its column means at every call, eager or replayed: the
+    # same launches, bit for bit; FP64 replays recompute them where the eager
+    # calls carry them, which differs by rounding only
+    tol = 0.0 if prec == agcm.AGCM_FP32 else 1e-13
+    for f in FIELDS:
+        assert np.abs(got[f] - want[f]).max() <= tol * np.abs(want[f]).max(), f
+    a.close()
+    b.close()

@@ -159,57 +159,64 @@ def cpu_oracle_rate(nlon, nlat, nlev, steps=1, st=None):
     return nlon * nlat * nlev * steps / el, el
 
 
-def _oracle_sample_step(arg):
-    """One FP64 oracle step of a seeded sample grid (runs in a worker process)."""
-    nlon, nlat, nlev, seed = arg
-    import oracle
-    from paper_2103_10114_gb300 import inputs
+_SAMPLE = {}
 
-    st = inputs.baroclinic_jet(nlon, nlat, nlev, seed=seed, noise=1e-2, terrain_seed=2)
-    o = oracle.Oracle(nlon, nlat, nlev, phis=st["phis"])
+
+def _oracle_sample_step(arg):
+    """One FP64 oracle step of a seeded sample grid in a worker process; the
+    sample and the oracle's grid are kept per worker, and only the step is
+    timed."""
+    nlon, nlat, nlev, seed = arg
+    key = (nlon, nlat, nlev, seed)
+    if key not in _SAMPLE:
+        import oracle
+        from paper_2103_10114_gb300 import inputs
+
+        _SAMPLE.clear()
+        st = inputs.baroclinic_jet(nlon, nlat, nlev, seed=seed, noise=1e-2, terrain_seed=2)
+        _SAMPLE[key] = (oracle.Oracle(nlon, nlat, nlev, phis=st["phis"]), st)
+    o, st = _SAMPLE[key]
     t0 = time.perf_counter()
     o.step(st, 60.0, 1)
     return time.perf_counter() - t0
 
 
-def cpu_oracle_rate_all_cores(nlon=360, nlat=180, nlev=30):
-    """The oracle as it stands, one independent sample step per host core in
-    spawned worker processes; returns (aggregate gp-steps/s, workers, wall s)."""
+def cpu_oracle_rate_all_cores(nlon=360, nlat=180, nlev=30, steps=1, warmup=1):
+    """The oracle as it stands, one sample step per host core at a time in
+    spawned worker processes; returns (aggregate gp-steps/s, workers, mean
+    seconds per step).  A step's time is that of its slowest worker."""
     import multiprocessing as mp
 
     import oracle
 
     oracle.build()  # compile once before the workers load it
     n = os.cpu_count() or 1
+    task = [(nlon, nlat, nlev, 100)] * n
     ctx = mp.get_context("spawn")
     with ctx.Pool(n) as pool:
-        pool.map(_oracle_sample_step, [(16, 8, 2, 0)] * n)  # workers up, library loaded
-        t0 = time.perf_counter()
-        pool.map(_oracle_sample_step, [(nlon, nlat, nlev, 100 + q) for q in range(n)])
-        wall = time.perf_counter() - t0
-    return n * nlon * nlat * nlev / wall, n, wall
+        for _ in range(max(1, warmup)):
+            pool.map(_oracle_sample_step, task, chunksize=1)
+        per_step = [max(pool.map(_oracle_sample_step, task, chunksize=1)) for _ in range(steps)]
+    el = sum(per_step)
+    return n * nlon * nlat * nlev * steps / el, n, el / steps
 
 
 def run_reference(args):
+    """The oracle on the machine's host cores: each timed step is one oracle step
+    of a 360x180x30 sample of the workload on every core at once."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     sample = (360, 180, 30)
-    for _ in range(args.warmup):
-        cpu_oracle_rate(*sample)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        cpu_oracle_rate(*sample)
-    el = time.perf_counter() - t0
-    pts = sample[0] * sample[1] * sample[2]
-    value = pts * args.steps / el
+    value, cores, sec = cpu_oracle_rate_all_cores(*sample, steps=args.steps, warmup=args.warmup)
     line = {
         "impl": "reference", "metric": "grid-point-steps/s", "value": value, "unit": "gp-steps/s",
-        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "leap-format IAP step 1440x720x30 (0.25 deg) jet+terrain", "sample": "360x180x30"},
-        "cpu_baseline": {"value": value, "unit": "gp-steps/s", "cores": 1, "kind": "oracle",
-                         "sample": "one oracle step of the same model on 360x180x30 per timed step"},
+        "config": {"workload": "leap-format IAP step 1440x720x30 (0.25 deg) jet+terrain",
+                   "sample": f"360x180x30 per core, {cores} cores"},
+        "cpu_baseline": {"value": value, "unit": "gp-steps/s", "cores": cores, "kind": "oracle",
+                         "sample": f"one oracle step of a 360x180x30 sample on each of {cores} cores per timed step"},
         "e2e": {"value": value, "unit": "gp-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -355,11 +362,11 @@ def main():
                                 "sample": f"one FP64 oracle step of the full {I}x{J}x{K} workload ({el:.1f} s)",
                                 "host_cores": os.cpu_count()}
         try:
-            arate, nw, wall = cpu_oracle_rate_all_cores()
+            arate, nw, sec = cpu_oracle_rate_all_cores(steps=2)
             line["cpu_baseline_all_cores"] = {
                 "value": arate, "unit": "gp-steps/s", "cores": nw, "kind": "oracle",
-                "sample": f"{nw} worker processes, one FP64 oracle step of a 360x180x30 sample each "
-                          f"({wall:.1f} s wall)"}
+                "sample": f"{nw} worker processes, one FP64 oracle step of a 360x180x30 sample each, "
+                          f"2 timed steps ({sec:.2f} s per step)"}
         except Exception as e:  # reported, not hidden
             line["cpu_baseline_all_cores"] = {"error": repr(e)}
     if rank == 0:

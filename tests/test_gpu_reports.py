@@ -77,3 +77,31 @@ def test_config5_1000_steps_fp32_drift():
     assert b["finite"] == 1
     assert abs(report["mass_drift"]) < 1e-5
     assert report["energy_drift"] < 0  # the three-stage step only removes energy
+
+
+def test_full_model_options_300_split_steps_fp32():
+    """1440 x 720 x 30 FP32 with every option the library has on at once: the
+    lapse-rate standard atmosphere with the delta kappa Phi/P term, split
+    stepping (adaptation sub-steps under the gravity-wave dt) and the
+    low-latitude filters after every step; 300 steps (about 10.7 simulated
+    hours).  Reports mass and energy drift; the run must stay finite and keep
+    its mass."""
+    I, J, K, n = 1440, 720, 30, 300
+    th = dict(profile=1, Ts0=288.15, lapse=6.5e-3, Ttrop=216.65, delta=1.0)
+    st = inputs.baroclinic_jet(I, J, K, seed=5, noise=1e-3, terrain_seed=2)
+    g = agcm.Grid(I, J, K, phis=st["phis"], thermo=th)
+    dt, msub = g.dt_split(100.0)
+    s = agcm.State(g, agcm.AGCM_FP32)
+    s.load(st)
+    a = s.diagnostics()
+    for _ in range(n):
+        s.step_split(1, dt, msub)
+        s.filter(0.25)
+    b = s.diagnostics()
+    report = {"grid": [I, J, K], "steps": n, "dt_s": dt, "msub": msub, "simulated_hours": n * dt / 3600,
+              "mass_drift": b["mass"] / a["mass"] - 1, "energy_drift": b["energy"] / a["energy"] - 1,
+              "finite": b["finite"], "max_u": b["max_u"], "max_v": b["max_v"]}
+    print("\nFULL_OPTIONS_REPORT " + json.dumps(report))
+    assert b["finite"] == 1
+    assert abs(report["mass_drift"]) < 1e-5
+    assert b["max_u"] < 200.0

@@ -8,8 +8,17 @@ full three-stage time step.  The metric is grid-point-steps per second
 (nlon*nlat*nlev*steps / s); for N > 1 each rank advances its own replica
 (the path has no exchange step on one GPU) and the value is the sum over ranks.
 
+The JSON line adds the roofline of the dominant kernel (algorithmic bytes over
+its CUDA-event launch time, against the measured copy bandwidth, with the ncu
+DRAM traffic of the same source), its instruction counters, the end-to-end
+rate through the C ABI with host buffers, the oracle's CPU rate on one and on
+all host cores, nvidia-smi clocks sampled during the timed region, and the
+other forms (FP64, small grid, split stepping, thermodynamics, filters, the
+64-member ensemble, the adjoint).
+
 The reference arm (--impl reference) times the FP64 CPU oracle, as it stands,
-on a bounded sample of the same workload (the same model on a coarser grid).
+on every host core, one 360x180x30 sample of the same model per core per
+timed step.
 """
 from __future__ import annotations
 

@@ -119,3 +119,22 @@ def test_fp32_adjoint_close_to_fp64_oracle():
     for f in FIELDS:
         err = np.abs(jtl[f] - ref[f]).max() / np.abs(ref[f]).max()
         assert err <= 1e-4, (f, err)
+
+
+def test_dot_product_fp64_config3_size():
+    """The dot test at the differentiation configuration's full size
+    (720 x 360 x 30, jet over terrain): <lam, J v> from the oracle's exact
+    tangent-linear step against <J^T lam, v> from the GPU adjoint."""
+    I, J, K = 720, 360, 30
+    g, o, x = setup(I, J, K, 21, kind="jet")
+    dt = g.dt(100.0)
+    s = agcm.State(g, agcm.AGCM_FP64)
+    s.load(x)
+    v = inputs.random_direction(I, J, K, seed=131)
+    lam = inputs.random_direction(I, J, K, seed=231)
+    _, jv = o.step_jvp(x, v, dt, 1)
+    jtl = to_np(s.step_adjoint(lam, dt))
+    lhs, rhs = dot(lam, jv), dot(jtl, v)
+    scale = max(absdot(lam, jv), absdot(jtl, v))
+    assert abs(lhs - rhs) <= 1e-12 * scale, (lhs, rhs, scale)
+    s.close()

@@ -122,3 +122,42 @@ def test_autotune_picks_a_shape_and_keeps_state():
         for f in FIELDS:
             assert np.array_equal(a[f], b[f])
     ens.close()
+
+
+def test_config4_full_mix_sampled_members():
+    """Config 4 as the bench runs it (64 members: 32 at 256x128x30, 24 at
+    360x180x30, 8 at 720x360x30, FP32; autotuned shape, CUDA-graph replay):
+    after two steps, one member of each size equals its own single-state run,
+    and the first member matches the FP64 oracle within the FP32 tolerance."""
+    import torch
+
+    import oracle
+
+    mix = [(256, 128, 30)] * 32 + [(360, 180, 30)] * 24 + [(720, 360, 30)] * 8
+    mem = members(agcm.AGCM_FP32, mix=mix, seed0=100)
+    ens = Ensemble([m[1] for m in mem])
+    dts = [m[3] for m in mem]
+    ens.autotune(dts, steps=1)
+    graph = ens.capture(2, dts)
+    graph.replay()
+    torch.cuda.synchronize()
+    ens.status()
+    for q in (0, 40, 63):
+        g, s, st, dt = mem[q]
+        got = np_state(s)
+        alone = agcm.State(g, agcm.AGCM_FP32)
+        alone.load(st)
+        alone.step(2, dt)
+        want = np_state(alone)
+        for f in FIELDS:
+            err = np.abs(got[f] - want[f]).max() / np.abs(want[f]).max()
+            assert err <= 1e-6, (q, f, err)
+        alone.close()
+    g, s, st, dt = mem[0]
+    o = oracle.Oracle(g.nlon, g.nlat, g.nlev, phis=st["phis"])
+    ref = o.step(st, dt, 2)
+    got = np_state(s)
+    for f in FIELDS:
+        err = np.abs(got[f] - ref[f]).max() / np.abs(ref[f]).max()
+        assert err <= 1e-5, (f, err)
+    ens.close()

@@ -239,7 +239,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
-    ap.add_argument("--only", choices=["adjoint", "ensemble", "fp64", "fp32_720", "split", "filter", "thermo"],
+    ap.add_argument("--only", choices=["adjoint", "ensemble", "fp64", "fp32_720", "split", "filter", "thermo", "gradient"],
                     help="measure one form alone and print its JSON (for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -438,6 +438,8 @@ def run_only(form):
         out = measure_filter(agcm, inputs, torch, reps=3)
     elif form == "thermo":
         out = measure_thermo(agcm, inputs, torch, steps=3)
+    elif form == "gradient":
+        out = measure_gradient(agcm, inputs, torch)
     else:  # fp64: the plain FP64 step at the bench size; fp32_720: FP32 at 720x360x30
         I, J, K = WORKLOAD if form == "fp64" else (720, 360, 30)
         st = inputs.baroclinic_jet(I, J, K, seed=6, noise=1e-2, terrain_seed=2)
@@ -511,6 +513,10 @@ def measure_forms(agcm, inputs, torch, steps=5):
         out["ensemble_64"] = measure_ensemble(agcm, inputs, torch)
     except Exception as e:  # reported, not hidden
         out["ensemble_64"] = {"error": repr(e)}
+    try:
+        out["gradient_config3"] = measure_gradient(agcm, inputs, torch)
+    except Exception as e:
+        out["gradient_config3"] = {"error": repr(e)}
     try:
         out["adjoint_720x360x30"] = measure_adjoint(agcm, inputs, torch)
     except Exception as e:
@@ -653,6 +659,40 @@ def measure_ensemble(agcm, inputs, torch, steps=10, per_member=True):
     res["speedup_vs_per_member_fp64"] = ms64 / ms
     for s in s64:
         s.close()
+    return res
+
+
+def measure_gradient(agcm, inputs, torch):
+    """Config 3 end to end: the gradient of J = mean pi^2 over a 20 x 20 deg box
+    after 50 FP32 steps at 720x360x30 with respect to the initial state,
+    through torch.autograd with 8 checkpointed states (forward, then the
+    binomial reverse sweep of adjoint steps and recomputation)."""
+    from paper_2103_10114_gb300 import autograd as ag
+
+    I, J, K, n = 720, 360, 30, 50
+    st = inputs.baroclinic_jet(I, J, K, seed=3, noise=1e-2, terrain_seed=2)
+    g = agcm.Grid(I, J, K, phis=st["phis"])
+    dt = g.dt(100.0)
+    s = agcm.State(g, agcm.AGCM_FP32)
+    mask = ag.box_mask(I, J)
+    x0 = {f: torch.as_tensor(st[f], dtype=torch.float32, device="cuda").requires_grad_(True)
+          for f in agcm.FIELDS}
+    times = []
+    for rep in range(2):  # the first run warms up
+        for v in x0.values():
+            v.grad = None
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = ag.run(s, x0, n, dt, snaps=8)
+        jval = ag.box_objective(out["pi"], mask)
+        jval.backward()
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    stats = getattr(ag.AgcmSteps, "last_stats", {})
+    res = {"seconds": times[-1], "steps": n, "snapshots": 8, "grid": [I, J, K],
+           "forward_steps_in_sweep": stats.get("forward_steps"), "max_snapshots": stats.get("max_snapshots"),
+           "grad_finite": bool(all(torch.isfinite(v.grad).all() for v in x0.values()))}
+    s.close()
     return res
 
 

@@ -167,3 +167,28 @@ def test_ensemble_member_with_lapse_profile():
         assert rel_err(out[f], ref[f]) <= 1e-12, f
     ens.close()
     s.close()
+
+
+def test_terrain_above_the_tropopause():
+    """Terrain scaled to 15 km puts some columns' standard surface above the
+    11 km tropopause (the isothermal branch of the standard atmosphere): the
+    library's surface tables still match the oracle's, through one step."""
+    I, J, K = 64, 32, 8
+    st = inputs.baroclinic_jet(I, J, K, seed=3, noise=1e-2, terrain_seed=2)
+    phis = st["phis"] * 5.0
+    assert phis.max() / 9.80665 > 11000.0
+    g = agcm.Grid(I, J, K, phis=phis, thermo=FULL)
+    o = oracle.Oracle(I, J, K, phis=phis, thermo=FULL)
+    x = {f: st[f] for f in FIELDS}
+    dt = g.dt(100.0)
+    ref = o.step(x, dt, 1)
+    d_ref = o.diagnostics(x)
+    s = agcm.State(g, agcm.AGCM_FP64)
+    s.load(x)
+    d = s.diagnostics()
+    assert abs(d["e_ps"] - d_ref["e_ps"]) <= 1e-12 * abs(d_ref["e_ps"])
+    s.step(1, dt)
+    out = to_np(s.store())
+    for f in FIELDS:
+        assert rel_err(out[f], ref[f]) <= 1e-12, f
+    s.close()

@@ -17,7 +17,8 @@
  *    colatitude (south).
  *  - Layout: SoA, row-major [k][j][i] with i (longitude) contiguous.
  *    U, Phi: K*J*I values; V: K*(J-1)*I; pi: J*I (= p'_sa / p0, the surface
- *    pressure anomaly over the standard pressure exp(-phi_s/(R*250 K))).
+ *    pressure anomaly over the grid's standard surface pressure pi~, which
+ *    is exp(-phi_s/(R*250 K)) by default; see agcm_grid_set_thermo).
  *  - Element type: double for AGCM_FP64 states, float for AGCM_FP32 states.
  *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = default
  *    stream).  Calls that take a stream are asynchronous on it unless stated.
@@ -154,8 +155,10 @@ int agcm_state_store(const agcm_state_t* state, void* U, void* V, void* Phi, voi
  * agcm_step — advance `nsteps` steps of length dt seconds with the
  * three-stage scheme x1 = xn + dt/2 T(xn), x2 = xn + dt/2 T(x1),
  * x_{n+1} = xn + dt T(x2) (three calls per step: Sec. "Optimizations").
- * T is the full spatial operator: leap advection, pressure gradient,
- * Coriolis, Omega~ conversion and the column-integrated divergence.
+ * T is the full spatial operator of Eq. 1 with the grid's thermodynamics:
+ * leap advection, pressure gradient, Coriolis, Omega~ conversion and the
+ * column-integrated divergence (Alg. 1 / Alg. 2).  nsteps >= 0 (0 does
+ * nothing), dt finite, else AGCM_EINVAL.
  * Asynchronous; launch errors are returned, device-side non-finite values
  * show up in agcm_diagnostics.
  */
@@ -186,8 +189,9 @@ int agcm_step_split(agcm_state_t* state, int nsteps, double dt, int msub, void* 
 int agcm_grid_dt_split(const agcm_grid_t* grid, double umax, double* dt, int* msub);
 
 /*
- * agcm_tendency — T(x) of the current state into caller-owned device
- * buffers (same layout and element type as the state).  For validation.
+ * agcm_tendency — T(x) of the current state (Eq. 2: -L + A) into
+ * caller-owned device buffers of the state's layout and element type; the
+ * state is not modified.  For validation.
  */
 int agcm_tendency(agcm_state_t* state, void* tU, void* tV, void* tPhi, void* tpi, void* stream);
 
@@ -207,7 +211,7 @@ typedef struct agcm_diag {
   double mass;      /* sum_j A_j (pi~ + pi)  [p0 m^2] */
   double e_kin;     /* 1/2 sum dsigma (A U^2 + Av V^2) */
   double e_pot;     /* 1/2 sum dsigma A Phi^2 (available potential) */
-  double e_ps;      /* 1/2 sum A (R T0 / pi~) pi^2 (available surface potential) */
+  double e_ps;      /* 1/2 sum A (R T~_s / pi~) pi^2 (available surface potential) */
   double energy;    /* e_kin + e_pot + e_ps */
   double max_u;     /* max |U| */
   double max_v;     /* max |V| */

@@ -105,3 +105,26 @@ def test_full_model_options_300_split_steps_fp32():
     assert b["finite"] == 1
     assert abs(report["mass_drift"]) < 1e-5
     assert b["max_u"] < 200.0
+
+
+def test_fp32_column_means_over_one_long_call():
+    """FP32 keeps the FP64 column means within a call by adding FP32 sums of
+    each stage's increments, and recomputes them exactly at the start of every
+    call: 2000 steps in one call end where 20 calls of 100 steps end, to within
+    the FP32 precision of the fields."""
+    I, J, K, n = 256, 128, 30, 2000
+    st = inputs.baroclinic_jet(I, J, K, seed=3, noise=1e-3, terrain_seed=2)
+    g = agcm.Grid(I, J, K, phis=st["phis"])
+    dt = g.dt(100.0)
+    a, b = agcm.State(g, agcm.AGCM_FP32), agcm.State(g, agcm.AGCM_FP32)
+    a.load(st)
+    b.load(st)
+    a.step(n, dt)
+    for _ in range(20):
+        b.step(n // 20, dt)
+    x, y = to_np(a.store()), to_np(b.store())
+    err = {f: float(np.abs(x[f] - y[f]).max() / np.abs(y[f]).max()) for f in FIELDS}
+    print("\nCOLUMN_MEANS_REPORT " + json.dumps({"steps": n, "one_call_vs_20_calls": err}))
+    assert max(err.values()) < 1e-4, err
+    a.close()
+    b.close()

@@ -224,7 +224,7 @@ struct agcm_state {
 namespace {
 
 template <class T>
-int upload_geom(agcm_grid* g, int p) {
+int upload_geom(const agcm_grid* g, void** blob_out, agcm::Geom<T>* geom_out) {
   const int I = g->I, J = g->J, K = g->K;
   // pack every table into one allocation
   std::vector<char> host;
@@ -349,26 +349,50 @@ int upload_geom(agcm_grid* g, int p) {
   G.rho = (const T*)(base + o_rho);
   G.nl = g->beta2 != 0.0 && g->th.delta != 0.0;
   G.rady = (T)(1.0 / (kA * g->dth));
-  g->dev[p].blob = d;
-  g->dev[p].ready = true;
-  if constexpr (sizeof(T) == 8)
-    g->gd = G;
-  else
-    g->gf = G;
+  *blob_out = d;
+  *geom_out = G;
   return AGCM_OK;
 }
 
 int ensure_geom(const agcm_grid* cg, int prec) {
   agcm_grid* g = const_cast<agcm_grid*>(cg);
-  std::lock_guard<std::mutex> lk(g_grid_mu);
   int dev = 0;
   CUDA_TRY(cudaGetDevice(&dev));
-  if (g->dev[prec].ready) {
-    if (g->device != dev) return fail(AGCM_EINVAL, "grid tables live on device %d, current device is %d", g->device, dev);
-    return AGCM_OK;
+  {
+    std::lock_guard<std::mutex> lk(g_grid_mu);
+    if (g->dev[prec].ready) {
+      if (g->device != dev)
+        return fail(AGCM_EINVAL, "grid tables live on device %d, current device is %d", g->device, dev);
+      return AGCM_OK;
+    }
+    if (g->device >= 0 && g->device != dev)
+      return fail(AGCM_EINVAL, "grid tables live on device %d, current device is %d", g->device, dev);
   }
-  g->device = dev;
-  return prec == AGCM_FP64 ? upload_geom<double>(g, prec) : upload_geom<float>(g, prec);
+  // The upload allocates through the allocator hook, which may call back into
+  // the embedding runtime (and from there into this library, e.g. a garbage
+  // collector destroying another state): it runs without the lock held.
+  void* blob = nullptr;
+  agcm::Geom<double> gd{};
+  agcm::Geom<float> gf{};
+  int rc = prec == AGCM_FP64 ? upload_geom<double>(g, &blob, &gd) : upload_geom<float>(g, &blob, &gf);
+  if (rc) return rc;
+  bool lost = false;
+  {
+    std::lock_guard<std::mutex> lk(g_grid_mu);
+    if (g->dev[prec].ready) {
+      lost = true;  // another thread published first
+    } else {
+      g->device = dev;
+      g->dev[prec].blob = blob;
+      if (prec == AGCM_FP64)
+        g->gd = gd;
+      else
+        g->gf = gf;
+      g->dev[prec].ready = true;
+    }
+  }
+  if (lost) dev_free(blob);
+  return AGCM_OK;
 }
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
@@ -685,10 +709,14 @@ int agcm_grid_create(int nlon, int nlat, int nlev, const double* sigma_half, con
 
 int agcm_grid_destroy(agcm_grid_t* g) {
   if (!g) return AGCM_OK;
-  std::lock_guard<std::mutex> lk(g_grid_mu);
-  if (g->refs > 0) return fail(AGCM_EINVAL, "grid still has %d live states", g->refs);
-  for (auto& d : g->dev)
-    if (d.blob) dev_free(d.blob);
+  void* blobs[2] = {nullptr, nullptr};
+  {
+    std::lock_guard<std::mutex> lk(g_grid_mu);
+    if (g->refs > 0) return fail(AGCM_EINVAL, "grid still has %d live states", g->refs);
+    for (int p = 0; p < 2; ++p) blobs[p] = g->dev[p].blob;
+  }
+  for (void* b : blobs)
+    if (b) dev_free(b);  // outside the lock: the free hook may call back into the library
   delete g;
   return AGCM_OK;
 }

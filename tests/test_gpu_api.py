@@ -167,3 +167,43 @@ def test_step_graph_replay_equals_eager_calls(prec):
         assert np.abs(got[f] - want[f]).max() <= tol * np.abs(want[f]).max(), f
     a.close()
     b.close()
+
+
+@pytest.mark.timeout(120, method="thread")
+def test_garbage_collection_inside_the_allocator_hook():
+    """The allocator hook may run arbitrary code of the embedding runtime, and
+    a garbage collector there may destroy other states and grids through this
+    library.  The library must not hold its grid lock across the hook: here a
+    state kept alive only by a reference cycle is collected from inside the
+    allocations that build a new grid's device tables."""
+    import gc
+
+    import torch
+
+    L = agcm.lib()
+    g0 = agcm.Grid(32, 16, 3)
+    s0 = agcm.State(g0, agcm.AGCM_FP32)
+    s0.cycle = s0  # only the cyclic collector can free it
+    del s0, g0
+    collected = {"n": 0}
+
+    def alloc(n, ctx):
+        collected["n"] += gc.collect()
+        return torch.cuda.caching_allocator_alloc(int(n))
+
+    def free(p, ctx):
+        gc.collect()
+        torch.cuda.caching_allocator_delete(p)
+
+    A, F = agcm._ALLOC_T(alloc), agcm._FREE_T(free)
+    agcm.check(L.agcm_set_allocator(ctypes.cast(A, ctypes.c_void_p), ctypes.cast(F, ctypes.c_void_p), None))
+    try:
+        g1 = agcm.Grid(40, 20, 3)
+        s1 = agcm.State(g1, agcm.AGCM_FP32)  # the grid upload allocates first
+        s1.close()
+        g1.close()
+        assert collected["n"] > 0
+    finally:
+        agcm.check(L.agcm_set_allocator(None, None, None))
+        agcm._alloc_cbs = None
+        agcm.use_torch_allocator()

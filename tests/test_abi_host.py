@@ -149,3 +149,49 @@ def test_thermo_dt_and_validation(L):
         with pytest.raises(agcm.AgcmError) as e:
             g.set_thermo(**bad)
         assert e.value.code == agcm.AGCM_EINVAL
+
+
+def test_header_is_c99_and_links_from_c(L, tmp_path):
+    """The boundary is a C ABI: a C99 program includes the header with every
+    warning as an error, links against the library and calls its host-only
+    entry points (grid geometry, Eq. 7 tables, the dt rule, errors)."""
+    import shutil
+    import subprocess
+
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "abi.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include "agcm.h"
+int main(void) {
+  agcm_grid_t* g = NULL;
+  int32_t lu[64], lv[63];
+  double dt = 0.0;
+  int msub = 0;
+  agcm_thermo_t th = {1, 250.0, 288.15, 6.5e-3, 216.65, 0.0, 0.0, 0.0};
+  if (agcm_version() <= 0) return 1;
+  if (agcm_grid_create(128, 64, 8, NULL, NULL, NULL, NULL, &g) != AGCM_OK) return 2;
+  if (agcm_grid_leap(g, lu, lv) != AGCM_OK || lu[0] < lu[32]) return 3;
+  if (agcm_grid_set_thermo(g, &th) != AGCM_OK) return 4;
+  if (agcm_grid_dt(g, 100.0, &dt) != AGCM_OK || !(dt > 0.0)) return 5;
+  if (agcm_grid_dt_split(g, 100.0, &dt, &msub) != AGCM_OK || msub < 1) return 6;
+  if (agcm_grid_destroy(g) != AGCM_OK) return 9;
+  if (agcm_grid_create(2, 64, 8, NULL, NULL, NULL, NULL, &g) != AGCM_EINVAL || g != NULL) return 7;
+  if (agcm_last_error()[0] == '\0') return 8;
+  printf("%d %g %d\n", lu[0], dt, msub);
+  return 0;
+}
+''')
+    inc = os.path.join(os.path.dirname(HEADER))
+    libdir = os.path.dirname(agcm.LIB_PATH)
+    exe = tmp_path / "abi"
+    cmd = [gcc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", inc, str(src), "-o", str(exe),
+           "-L", libdir, "-l:" + os.path.basename(agcm.LIB_PATH), "-Wl,-rpath," + libdir]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
+    first, dt, msub = r.stdout.split()
+    assert int(first) > 1 and float(dt) > 0 and int(msub) >= 1

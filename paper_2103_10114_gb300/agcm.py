@@ -278,11 +278,24 @@ class State:
         self._last_load = ts  # keep alive until the copy is done
         return self
 
+    def _check_host(self, host):
+        """The copies read or write whole fields through raw pointers: every host
+        tensor must be a contiguous CPU tensor of the state's dtype and size."""
+        shapes = self.grid.shapes()
+        for f in FIELDS:
+            t = host[f]
+            n = int(np.prod(shapes[f]))
+            if t.device.type != "cpu" or t.dtype != self.dtype or not t.is_contiguous() or t.numel() != n:
+                raise ValueError(f"host field {f}: need a contiguous CPU {self.dtype} tensor of {n} values, "
+                                 f"got {t.device} {t.dtype} with {t.numel()} values")
+
     def load_host(self, host, stream=None):
-        """host: dict of pinned CPU tensors of the state's dtype (e2e path)."""
+        """host: dict of CPU tensors of the state's dtype (pinned for asynchronous copies)."""
+        self._check_host(host)
         check(lib().agcm_state_load(self._h, *[host[f].data_ptr() for f in FIELDS], 0, _stream_ptr(stream)))
 
     def store_host(self, host, stream=None):
+        self._check_host(host)
         check(lib().agcm_state_store(self._h, *[host[f].data_ptr() for f in FIELDS], 0, _stream_ptr(stream)))
 
     def store(self, stream=None):

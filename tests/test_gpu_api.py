@@ -207,3 +207,23 @@ def test_garbage_collection_inside_the_allocator_hook():
         agcm.check(L.agcm_set_allocator(None, None, None))
         agcm._alloc_cbs = None
         agcm.use_torch_allocator()
+
+
+def test_host_copies_reject_wrong_buffers():
+    import torch
+
+    I, J, K = 32, 16, 3
+    g = agcm.Grid(I, J, K)
+    s = agcm.State(g, agcm.AGCM_FP32)
+    good = {f: torch.zeros(sh, dtype=torch.float32) for f, sh in g.shapes().items()}
+    s.load_host(good)
+    s.store_host(good)
+    bad_size = dict(good, U=torch.zeros(K * J * I - 1, dtype=torch.float32))
+    bad_type = dict(good, Phi=torch.zeros(g.shapes()["Phi"], dtype=torch.float64))
+    bad_dev = dict(good, pi=torch.zeros(g.shapes()["pi"], dtype=torch.float32, device="cuda"))
+    for bad in (bad_size, bad_type, bad_dev):
+        with pytest.raises(ValueError):
+            s.load_host(bad)
+        with pytest.raises(ValueError):
+            s.store_host(bad)
+    s.close()

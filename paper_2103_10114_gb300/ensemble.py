@@ -1,13 +1,22 @@
 """Ensembles of members of uneven resolution: one persistent launch per call,
 an autotuner for its launch shape, and CUDA-graph replay.
 
-The launch shape (one-warp blocks, how many resident per SM) and the row tile
-of a work item (32 columns of 1, 2 or 4 consecutive rows, taken in order by one
-warp) decide how the work is spread over the SMs, how many warps hide each
-other's memory latency and how much of a row's stencil is still in L1 for the
-next row; the best choice depends on the member mix and the GPU, so
-`autotune` times each candidate on the ensemble itself and keeps the fastest
-(cached per member mix and device name for the life of the process).
+Two ways to advance the members, both captured whole in one CUDA graph:
+
+* "persistent": one launch of the ensemble kernel (agcm_ensemble_step); its
+  launch shape (one-warp blocks, how many resident per SM) and the row tile of
+  a work item (32 columns of 1, 2 or 4 consecutive rows, taken in order by one
+  warp) decide how the work spreads over the SMs and how many warps hide each
+  other's memory latency;
+* "streams": each member stepped by the single-state kernel (agcm_step) with
+  the members spread round-robin over N CUDA streams, so small members run
+  side by side.  The single-state kernel reads its grid tables from the launch
+  parameters and fits in 96 registers, where the persistent kernel, which
+  reads each member's tables through a descriptor, needs 168.
+
+The best choice depends on the member mix and the GPU, so `autotune` times
+each candidate on the ensemble itself and keeps the fastest (cached per
+member mix and device name for the life of the process).
 """
 from __future__ import annotations
 
@@ -26,6 +35,7 @@ class Ensemble:
         agcm.check(agcm.lib().agcm_ensemble_create(arr, len(self.states), ctypes.byref(h)))
         self._h = h
         self.shape = (1, 0, 1)
+        self._streams = []
 
     @property
     def handle(self):
@@ -34,8 +44,18 @@ class Ensemble:
     def points(self):
         return sum(s.grid.points() for s in self.states)
 
-    def configure(self, warps_per_block, blocks_per_sm, rows_per_item=1):
-        """Launch shape and row tile: (warps per block, blocks per SM, rows per item)."""
+    def configure(self, warps_per_block, blocks_per_sm=0, rows_per_item=1):
+        """Persistent launch: (warps per block, blocks per SM, rows per item).
+        Streams: configure("streams", n) steps the members on n streams."""
+        if warps_per_block == "streams":
+            import torch
+
+            n = int(blocks_per_sm)
+            if n < 1:
+                raise ValueError("need at least one stream")
+            self._streams = [torch.cuda.Stream() for _ in range(n)]
+            self.shape = ("streams", n)
+            return
         agcm.check(agcm.lib().agcm_ensemble_configure(self._h, int(warps_per_block), int(blocks_per_sm)))
         agcm.check(agcm.lib().agcm_ensemble_tile(self._h, int(rows_per_item)))
         self.shape = (int(warps_per_block), int(blocks_per_sm), int(rows_per_item))
@@ -44,8 +64,25 @@ class Ensemble:
         agcm.check(agcm.lib().agcm_ensemble_set_timeout(self._h, float(seconds), int(test_missing_blocks)))
 
     def step(self, nsteps, dts, stream=None):
+        if self.shape[0] == "streams":
+            self._step_streams(nsteps, dts, stream)
+            return
         arr = (ctypes.c_double * len(self.states))(*[float(d) for d in dts])
         agcm.check(agcm.lib().agcm_ensemble_step(self._h, int(nsteps), arr, agcm._stream_ptr(stream)))
+
+    def _step_streams(self, nsteps, dts, stream=None):
+        """Fork the members over the streams after `stream`, join them back."""
+        import torch
+
+        if nsteps == 0:
+            return
+        main = stream if stream is not None else torch.cuda.current_stream()
+        for q in self._streams:
+            q.wait_stream(main)
+        for k, (s, dt) in enumerate(zip(self.states, dts)):
+            s.step(int(nsteps), float(dt), stream=self._streams[k % len(self._streams)])
+        for q in self._streams:
+            main.wait_stream(q)
 
     def status(self, stream=None):
         """Synchronises; raises AgcmError(AGCM_ETIMEOUT) if a barrier gave up."""
@@ -76,6 +113,7 @@ class Ensemble:
             return _TUNE_CACHE[key], {}
         if candidates is None:
             candidates = [(1, b, r) for r in (1, 2, 4) for b in (0, 8, 16)]
+            candidates += [("streams", n) for n in (4, 8, 16)]
         saved = [s.store() for s in self.states]
         times = {}
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -99,8 +137,9 @@ class Ensemble:
         return best, times
 
     def capture(self, nsteps, dts):
-        """A CUDA graph of `nsteps` ensemble steps (one persistent launch);
-        replay it with graph.replay()."""
+        """A CUDA graph of `nsteps` ensemble steps (the persistent launch, or
+        the members' launches forked over the streams); replay it with
+        graph.replay()."""
         import torch
 
         self.step(0, dts)  # uploads dt and the vertical means outside the capture

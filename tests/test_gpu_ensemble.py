@@ -161,3 +161,30 @@ def test_config4_full_mix_sampled_members():
         err = np.abs(got[f] - ref[f]).max() / np.abs(ref[f]).max()
         assert err <= 1e-5, (f, err)
     ens.close()
+
+
+@pytest.mark.parametrize("prec", [agcm.AGCM_FP32, agcm.AGCM_FP64])
+def test_streams_mode_equals_single_runs_and_replays(prec):
+    """The streams mode steps every member with the single-state kernel, so
+    each member equals its own run bit for bit, eagerly and from a graph."""
+    import torch
+
+    mem = members(prec)
+    ens = Ensemble([m[1] for m in mem])
+    ens.configure("streams", 3)
+    dts = [m[3] for m in mem]
+    ens.step(2, dts)
+    graph = ens.capture(2, dts)
+    graph.replay()
+    torch.cuda.synchronize()
+    for g, s, st, dt in mem:
+        got = np_state(s)
+        alone = agcm.State(g, prec)
+        alone.load(st)
+        alone.step(2, dt)
+        alone.step(2, dt)
+        want = np_state(alone)
+        for f in FIELDS:
+            assert np.array_equal(got[f], want[f]), (g.nlon, f)
+        alone.close()
+    ens.close()

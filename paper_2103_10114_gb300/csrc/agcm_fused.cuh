@@ -10,7 +10,8 @@
 //           it is carried for the own column, the column to the east (U cell
 //           needs W at u and u+1) and the column to the south (V cell).
 //   * dS  — suffix sums of the *differences* of the hydrostatic integrand
-//           h_k' (b/P) Phi_k' between the two columns that enter each pressure
+//           beta_k' h_k' Phi_k' / P (the level coefficient beta of Eq. 1 sits
+//           in the tables) between the two columns that enter each pressure
 //           gradient (Eq. 6's pair for U, the j/j+1 pair for V), so psi is
 //           never needed away from the thread's own stencil, however wide the
 //           leap stride M_j is.
@@ -33,17 +34,12 @@ namespace agcm {
 // resident blocks requested (measured on GB300 at 1440x720x30: 20 one-warp
 // blocks per SM, i.e. <= 96 registers, is the fastest FP32 shape; FP64 is
 // bound by the FP64 pipe and keeps more registers).
-#ifndef AGCM_FUSED_BY
-#define AGCM_FUSED_BY 1
-#endif
 #ifndef AGCM_FUSED_MINB
 #define AGCM_FUSED_MINB 20
 #endif
 #ifndef AGCM_FUSED_MINB64
 #define AGCM_FUSED_MINB64 8
 #endif
-constexpr int kFusedBX = 32, kFusedBY = AGCM_FUSED_BY;
-
 // ---- shared-memory tile staged by the TMA bulk-copy engine
 constexpr int kTileX = 32, kTileY = 4;          // one block = 32 columns x 4 rows
 constexpr int kHaloMax = 64;                    // leap strides up to 63 are staged
@@ -159,6 +155,8 @@ __device__ __forceinline__ void tile_issue(const TileCtx<T>& t, const Geom<T>& g
 // TERMS selects the term groups of Eq. 2: 1 = advection L (skew flux form,
 // vertical advection), 2 = adaptation A (pressure gradient, Coriolis pair,
 // Omega~ conversion, dpi/dt), 3 = both (the unsplit step).
+// NL: Eq. 1's delta kappa Phi/P term is on; every Phi/P that enters psi or
+// the Omega~ coefficient is scaled by 1 + rho_k Phi/P.
 template <class T, int MODE, bool TILE, int TERMS = 3, bool NL = false>
 __device__ __forceinline__ void fused_column(
     const Geom<T>& g, const int i, const int j, const T* __restrict__ U, const T* __restrict__ V,

@@ -12,14 +12,18 @@
 //   k_adj_column   reverse of phase B (one thread per column): the column
 //                  integral C, the sigma mass flux W (Alg. 1 / Alg. 2), the
 //                  hydrostatic psi and the Omega~ term are linear in D and
-//                  B = (b/P) Phi, so their adjoints are the transposed prefix /
+//                  B = Phi / P (the level coefficient of Eq. 1 sits in the H
+//                  tables), so their adjoints are the transposed prefix /
 //                  suffix scans; D's adjoint is scattered to the fluxes.
+// The nonlinear delta kappa Phi/P term is not covered (the entry point
+// refuses it).
 //   k_adj_conv     F = P^u U, G = U / P^u, ... -> adjoints of U, V, Phi and the
 //                  2-D adjoints of P, P^u, P^v, folded into the adjoint of the
 //                  mass m = pi~ + pi.
 //   k_adj_colstate m^u, m^v are stride-1 means of m; gathers the adjoint of pi.
 //
-// Output: out = (accumulate ? out : 0) + scale * J(x)^T ybar.
+// Output: out = (accumulate ? out : 0) + scale * J(x)^T ybar, and optionally
+// sum += scale * J(x)^T ybar in the same pass (the stage accumulation).
 #pragma once
 #include "agcm_common.cuh"
 #include "agcm_phases.cuh"

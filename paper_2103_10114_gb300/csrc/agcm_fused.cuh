@@ -237,7 +237,7 @@ __device__ __forceinline__ void fused_column(
   const T PuvE = hasS ? Pu_at(rj, vfE) : T(0), PuvW = hasS ? Pu_at(rj, vfW) : T(0);
   const T PusvE = hasS ? Pu_at(rjp, vfE) : T(0), PusvW = hasS ? Pu_at(rjp, vfW) : T(0);
   const T PugE = hasS ? Pu_at(rjp, gE) : T(0), PugW = hasS ? Pu_at(rjp, gW) : T(0);
-  // R T0 pi / pi~ at the columns of the two pressure-gradient pairs
+  // R T~_s pi / pi~ at the columns of the two pressure-gradient pairs
   const T psE1 = g.rt0pit[rj + fE1] * pi[rj + fE1], psW1 = g.rt0pit[rj + fW1] * pi[rj + fW1];
   const T psc = g.rt0pit[rj + i] * pi[rj + i];
   const T pss = hasS ? g.rt0pit[rjp + i] * pi[rjp + i] : T(0);

@@ -7,7 +7,7 @@
 //                      the column sum C (FP64) that gives dpi/dt = -C, the
 //                      sigma mass flux W_h = sh_h C - sum_{k<h} dsigma D
 //                      (Alg. 1 / Alg. 2), the Omega~ term and the
-//                      hydrostatic psi = phi' + R T0 pi/pi~ (one thread per column,
+//                      hydrostatic psi = phi' + R T~_s pi/pi~ (one thread per column,
 //                      loops over k).
 //  phase C:            advection (skew form, zonal partners at +-M),
 //                      pressure gradient at the (x+N, x-N+1) pair, Coriolis

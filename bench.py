@@ -42,7 +42,7 @@ BYTES_PER_POINT_STEP = {4: 96, 8: 192}  # 24 words: stages read/write 6 + 9 + 9 
 # (profiles/), valid only while the kernel source is the one that was captured.
 NCU_TRAFFIC = {
     # kernel name: (sha1 of csrc/agcm_fused.cuh at capture time, bytes per launch, profile file)
-    "k_fused_stage": ("2bde3287819bc1773849f62653e4e6ec006da398", 1070104149,
+    "k_fused_stage": ("b984a3880f7cc8e094ddbc34b359a52f41a04ac5", 1070146560,
                       "profiles/fused_stage_1440x720x30_fp32.md"),
 }
 
@@ -52,7 +52,7 @@ NCU_TRAFFIC = {
 # (fadd + fmul + 2 ffma), thread instructions per point, warp instructions
 # issued per point.
 NCU_OPS = {
-    "k_fused_stage": ("2bde3287819bc1773849f62653e4e6ec006da398", 225.7, 527.1, 16.84,
+    "k_fused_stage": ("b984a3880f7cc8e094ddbc34b359a52f41a04ac5", 225.7, 527.1, 16.84,
                       "profiles/fused_stage_ops_720x360x30_fp32.md"),
 }
 

@@ -375,3 +375,24 @@ def test_operation_count_is_faithful_and_stride_free():
         assert min(ops.values()) > 0
         counts.append(ops)
     assert all(counts[1][k] == 2 * counts[0][k] for k in counts[0])
+
+
+@pytest.mark.parametrize("shift", [1, 3, 7])
+def test_zonal_translation_invariance(shift):
+    """Every longitude is treated alike: shifting all fields (U keeps its half
+    point offset) by s grid points shifts the tendency by s, bit for bit,
+    including across the periodic seam; random odd strides up to nlon/2 make
+    every leap offset wrap somewhere."""
+    I, J, K = 20, 9, 4
+    rng = np.random.default_rng(3)
+    mu = 2 * rng.integers(0, 5, J) + 1
+    mv = 2 * rng.integers(0, 5, J - 1) + 1
+    st = inputs.random_state(I, J, K, seed=8)
+    phis = np.asarray(st["phis"]).reshape(J, I)
+    o = oracle.Oracle(I, J, K, leap_u=mu, leap_v=mv, phis=phis)
+    o_s = oracle.Oracle(I, J, K, leap_u=mu, leap_v=mv, phis=np.roll(phis, shift, axis=-1))
+    x = state_only(st)
+    xs = {f: np.roll(v, shift, axis=-1) for f, v in x.items()}
+    t, ts = o.tendency(x), o_s.tendency(xs)
+    for f in FIELDS:
+        assert np.array_equal(np.roll(t[f], shift, axis=-1), ts[f]), f

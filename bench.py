@@ -41,18 +41,19 @@ BYTES_PER_POINT_STEP = {4: 96, 8: 192}  # 24 words: stages read/write 6 + 9 + 9 
 # DRAM traffic of the dominant kernel from an ncu capture of this workload
 # (profiles/), valid only while the kernel source is the one that was captured.
 NCU_TRAFFIC = {
-    # kernel name: (sha1 of csrc/agcm_fused.cuh at capture time, bytes per launch, profile file)
-    "k_fused_stage": ("b984a3880f7cc8e094ddbc34b359a52f41a04ac5", 1070146560,
+    # kernel name: (sha1 of csrc/agcm_fused.cuh at capture time, bytes per stage
+    # summed over the stage's launches, profile file)
+    "k_fused_stage": ("dfd644161e5064f99b3e443a75adeb3c89866f06", 1061100203,
                       "profiles/fused_stage_1440x720x30_fp32.md"),
 }
 
-# Instruction counters of the dominant kernel (ncu, 720x360x30 FP32, one launch
-# of each stage kind, averaged over the three stages), valid while the kernel
+# Instruction counters of the dominant kernel (ncu, 720x360x30 FP32, the launches
+# of each stage summed, averaged over the three stages), valid while the kernel
 # source is the one that was captured: FP32 flops per point and stage
 # (fadd + fmul + 2 ffma), thread instructions per point, warp instructions
 # issued per point.
 NCU_OPS = {
-    "k_fused_stage": ("b984a3880f7cc8e094ddbc34b359a52f41a04ac5", 225.7, 527.1, 16.84,
+    "k_fused_stage": ("dfd644161e5064f99b3e443a75adeb3c89866f06", 218.0, 460.1, 14.70,
                       "profiles/fused_stage_ops_720x360x30_fp32.md"),
 }
 
@@ -321,7 +322,12 @@ def main():
     # dominant kernel and its algorithmic bytes (one stage: 6/9/9 words per point -> 8 on average)
     name, (kms, kn) = max(prof.items(), key=lambda kv: kv[1][0])
     stage_bytes = pts * 8 * esz
-    achieved = stage_bytes / (kms / kn / 1e3) / 1e9 if name == "k_fused_stage" else None
+    # the profiler brackets each stage (the stride-1 row band and the other
+    # rows, two concurrent launches) with one pair of events: the roofline's
+    # unit is the stage
+    n_stages = 3 * args.steps
+    stage_ms = kms / n_stages
+    achieved = stage_bytes / (stage_ms / 1e3) / 1e9 if name == "k_fused_stage" else None
     traffic, traffic_src = None, None
     rec = NCU_TRAFFIC.get(name)
     if rec and rec[0] == kernel_source_hash():
@@ -332,7 +338,7 @@ def main():
         nsm = torch.cuda.get_device_properties(0).multi_processor_count
         fmax = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"]) \
             if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 2070.0
-        launch_s = kms / kn / 1e3
+        launch_s = stage_ms / 1e3
         fp32 = orec[1] * pts / launch_s / 1e12
         fp32_peak = nsm * 128 * 2 * fmax * 1e6 / 1e12
         issue = orec[3] * pts / launch_s
@@ -353,7 +359,8 @@ def main():
         "hbm_frac_step": value / world * BYTES_PER_POINT_STEP[esz] / (peak * 1e9),
         "roofline": {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic, "peak_kind": peak_kind,
-                     "traffic_source": traffic_src, "bytes_per_launch": stage_bytes, "avg_launch_ms": kms / kn,
+                     "traffic_source": traffic_src, "bytes_per_stage": stage_bytes, "avg_stage_ms": stage_ms,
+                     "launches_per_stage": kn / n_stages,
                      "note": "peak = measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},
         "compute": compute,
         "kernels": {k: {"ms_total": v[0], "launches": v[1], "share": v[0] / sum(x[0] for x in prof.values())}

@@ -22,6 +22,11 @@
  *  - Element type: double for AGCM_FP64 states, float for AGCM_FP32 states.
  *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = default
  *    stream).  Calls that take a stream are asynchronous on it unless stated.
+ *    A state also owns one internal stream: each stage of agcm_step,
+ *    agcm_step_split, agcm_tendency and agcm_step_adjoint forks part of its
+ *    rows onto it after the work already queued on `stream` and joins it back
+ *    before `stream` continues, so ordering on `stream` (and capture of
+ *    `stream` into a CUDA graph) is as for one launch.
  *  - Errors: every call returns AGCM_OK (0) or a negative-free positive code
  *    below; agcm_last_error() returns a message for the calling thread.  The
  *    library never aborts the process and never traps on the device.
@@ -226,6 +231,9 @@ int agcm_diagnostics(const agcm_state_t* state, agcm_diag_t* out, void* stream);
  * agcm_profile_enable(state, 1) clears the counters and starts recording;
  * agcm_profile_read synchronises the recorded events and returns, per kernel
  * id 0..agcm_kernel_count()-1, the summed milliseconds and the launch count.
+ * The events bracket a whole stage of the stage kernel, which is one launch
+ * or two concurrent ones (the stride-1 row band and the other rows): its
+ * milliseconds are per stage, its count is of launches.
  * ms_total and launches hold at least agcm_kernel_count() entries.
  */
 int agcm_profile_enable(agcm_state_t* state, int enable);

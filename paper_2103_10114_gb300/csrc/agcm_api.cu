@@ -145,7 +145,7 @@ static const char* const kKernelNames[KID_COUNT] = {
 
 struct Profiler {
   bool on = false;
-  struct Rec { int id; cudaEvent_t a, b; };
+  struct Rec { int id; cudaEvent_t a, b; int nl; };
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> pool;
   double ms[KID_COUNT] = {};
@@ -158,13 +158,16 @@ struct Profiler {
   }
   void begin(int id, cudaStream_t st) {
     if (!on) return;
-    Rec r{id, get(), get()};
+    Rec r{id, get(), get(), 1};
     cudaEventRecord(r.a, st);
     recs.push_back(r);
   }
-  void end(cudaStream_t st) {
+  // nlaunch: kernel launches inside the bracket (a stage of the stage kernel
+  // may be two concurrent launches)
+  void end(cudaStream_t st, int nlaunch = 1) {
     if (!on || recs.empty()) return;
     cudaEventRecord(recs.back().b, st);
+    recs.back().nl = nlaunch;
   }
   int drain() {
     for (auto& r : recs) {
@@ -172,7 +175,7 @@ struct Profiler {
       float t = 0.f;
       cudaEventElapsedTime(&t, r.a, r.b);
       ms[r.id] += t;
-      n[r.id] += 1;
+      n[r.id] += r.nl;
       pool.push_back(r.a);
       pool.push_back(r.b);
     }
@@ -211,6 +214,10 @@ struct agcm_state {
   // diagnostics partials
   double* diag = nullptr;
   int* err = nullptr;  // device status word: AGCM_ETIMEOUT if a bounded wait gave up
+  // the stage kernel's second launch (the stride-1 band) runs on aux, forked
+  // from and joined to the caller's stream by the two events
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::vector<void*> owned;
   // adjoint workspace (allocated on the first agcm_step_adjoint call)
   bool adj_ready = false;
@@ -222,6 +229,28 @@ struct agcm_state {
 };
 
 namespace {
+
+// The longest run of rows j, 1 <= j <= J-3, whose stencil strides Mu_j, Mv_j
+// and Mu_{j+1} are all 1 (the low-latitude band of Eq. 7): those rows run the
+// stride-1 column body.  Empty (lo = hi = 0) when there is none.
+inline void leap1_band(const agcm_grid* g, int* lo, int* hi) {
+  int best_lo = 0, best_hi = 0;
+  for (int j = 1; j <= g->J - 3;) {
+    if (g->Mu[j] == 1 && g->Mv[j] == 1 && g->Mu[j + 1] == 1) {
+      int e = j;
+      while (e <= g->J - 3 && g->Mu[e] == 1 && g->Mv[e] == 1 && g->Mu[e + 1] == 1) ++e;
+      if (e - j > best_hi - best_lo) {
+        best_lo = j;
+        best_hi = e;
+      }
+      j = e;
+    } else {
+      ++j;
+    }
+  }
+  *lo = best_lo;
+  *hi = best_hi;
+}
 
 template <class T>
 int upload_geom(const agcm_grid* g, void** blob_out, agcm::Geom<T>* geom_out) {
@@ -348,6 +377,7 @@ int upload_geom(const agcm_grid* g, void** blob_out, agcm::Geom<T>* geom_out) {
   G.pit = (const T*)(base + o_pit);
   G.rho = (const T*)(base + o_rho);
   G.nl = g->beta2 != 0.0 && g->th.delta != 0.0;
+  leap1_band(g, &G.l1lo, &G.l1hi);
   G.rady = (T)(1.0 / (kA * g->dth));
   *blob_out = d;
   *geom_out = G;
@@ -426,22 +456,53 @@ int ensure_bar(agcm_state* s, cudaStream_t st) {
 // (outb < 0: not written).
 // Launch of the stage kernel.  AGCM_STAGE_TILE selects the shape: 0 = one
 // warp per 32-column row segment with global loads (default: fastest on GB300
-// at 1440x720x30: 0.67 ms per stage against 0.96 ms for the tiles), 1 = 32 x 4
+// at 1440x720x30: 0.59 ms per stage against 0.96 ms for the tiles), 1 = 32 x 4
 // tiles staged by TMA.
 #ifndef AGCM_STAGE_TILE
 #define AGCM_STAGE_TILE 0
 #endif
+// Rows launch: the stride-1 band [l1lo, l1hi) with the specialised column
+// body and the other rows with the general one.  Given aux, evf and evj (a
+// second stream and two events), the band runs on aux, forked from st after
+// everything already queued there and joined back before st continues, so the
+// two launches overlap (each fills the other's tail); without them they run
+// one after the other on st.  *launched (optional) receives the number of
+// kernel launches made.
 template <class T, int MODE, int TERMS = 3>
 int launch_fused(const agcm::Geom<T>& G, const void* const xs[4], const double* ub, const double* vb,
                  const void* const xb[4], void* const out[4], double* ubo, double* vbo, const double* ubb,
-                 const double* vbb, double cdt, int* err, cudaStream_t st) {
+                 const double* vbb, double cdt, int* err, cudaStream_t st, cudaStream_t aux = nullptr,
+                 cudaEvent_t evf = nullptr, cudaEvent_t evj = nullptr, int* launched = nullptr) {
+  if (launched) *launched = 1;
   auto rows = [&](auto nl) -> int {  // one warp per 32 columns of a row
     const dim3 block(agcm::kTileX, 1);
-    const dim3 grid((unsigned)((G.I + agcm::kTileX - 1) / agcm::kTileX), (unsigned)G.J);
-    agcm::k_fused_stage<T, MODE, 1, TERMS, decltype(nl)::value><<<grid, block, 0, st>>>(
-        G, (const T*)xs[0], (const T*)xs[1], (const T*)xs[2], (const T*)xs[3], ub, vb, (const T*)xb[0],
-        (const T*)xb[1], (const T*)xb[2], (const T*)xb[3], (T*)out[0], (T*)out[1], (T*)out[2], (T*)out[3], ubo, vbo,
-        ubb, vbb, (T)cdt, 0, err);
+    const unsigned gx = (unsigned)((G.I + agcm::kTileX - 1) / agcm::kTileX);
+    const int nb = G.l1hi - G.l1lo;
+    auto go = [&](auto part, int ny, cudaStream_t q) {
+      agcm::k_fused_stage<T, MODE, 1, TERMS, decltype(nl)::value, decltype(part)::value>
+          <<<dim3(gx, (unsigned)ny), block, 0, q>>>(
+              G, (const T*)xs[0], (const T*)xs[1], (const T*)xs[2], (const T*)xs[3], ub, vb, (const T*)xb[0],
+              (const T*)xb[1], (const T*)xb[2], (const T*)xb[3], (T*)out[0], (T*)out[1], (T*)out[2], (T*)out[3],
+              ubo, vbo, ubb, vbb, (T)cdt, 0, err);
+    };
+    if (nb <= 0) {
+      go(std::integral_constant<int, 0>{}, G.J, st);
+    } else if (nb == G.J) {
+      go(std::integral_constant<int, 2>{}, nb, st);
+    } else {
+      const bool fork = aux && evf && evj;
+      if (fork) {
+        CUDA_TRY(cudaEventRecord(evf, st));
+        CUDA_TRY(cudaStreamWaitEvent(aux, evf, 0));
+      }
+      go(std::integral_constant<int, 2>{}, nb, fork ? aux : st);
+      go(std::integral_constant<int, 1>{}, G.J - nb, st);
+      if (fork) {
+        CUDA_TRY(cudaEventRecord(evj, aux));
+        CUDA_TRY(cudaStreamWaitEvent(st, evj, 0));
+      }
+      if (launched) *launched = 2;
+    }
     CUDA_TRY(cudaGetLastError());
     return AGCM_OK;
   };
@@ -479,10 +540,12 @@ template <class T, int MODE, int TERMS = 3>
 int fused_stage(agcm_state* s, int in, void* const out[4], int outb, double cdt, cudaStream_t st) {
   const agcm::Geom<T>& G = geom_of<T>(s);
   s->prof.begin(KID_FUSED, st);
+  int launched = 1;
   int rc = launch_fused<T, MODE, TERMS>(G, s->x[in], s->ubar[in], s->vbar[in], s->x[0], out,
                                  outb >= 0 ? s->ubar[outb] : nullptr, outb >= 0 ? s->vbar[outb] : nullptr,
-                                 s->ubar[0], s->vbar[0], cdt, s->err, st);
-  s->prof.end(st);
+                                 s->ubar[0], s->vbar[0], cdt, s->err, st, s->aux, s->ev_fork, s->ev_join,
+                                 &launched);
+  s->prof.end(st, launched);
   return rc;
 }
 
@@ -779,6 +842,14 @@ int agcm_grid_dt(const agcm_grid_t* g, double umax, double* dt) {
   return AGCM_OK;
 }
 
+static void release_streams(agcm_state* s) {
+  if (s->ev_join) cudaEventDestroy(s->ev_join);
+  if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+  if (s->aux) cudaStreamDestroy(s->aux);
+  s->ev_join = s->ev_fork = nullptr;
+  s->aux = nullptr;
+}
+
 int agcm_state_create(const agcm_grid_t* g, int precision, int nmembers, agcm_state_t** out) {
   if (!g || !out) return fail(AGCM_EINVAL, "null argument");
   *out = nullptr;
@@ -824,10 +895,15 @@ int agcm_state_create(const agcm_grid_t* g, int precision, int nmembers, agcm_st
       size_t n = f == 1 ? std::max<size_t>(s->nv, 1) : (f == 3 ? s->n2 : s->n3);
       cudaMemset(s->x[c][f], 0, n * s->esz);
     }
-  if (cudaDeviceSynchronize() != cudaSuccess) {
+  if (cudaStreamCreateWithFlags(&s->aux, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaDeviceSynchronize() != cudaSuccess) {
+    const cudaError_t e = cudaGetLastError();
+    release_streams(s);
     for (void* p : s->owned) dev_free(p);
     delete s;
-    return fail(AGCM_ECUDA, "state initialisation failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return fail(AGCM_ECUDA, "state initialisation failed: %s", cudaGetErrorString(e));
   }
   {
     std::lock_guard<std::mutex> lk(g_grid_mu);
@@ -840,6 +916,7 @@ int agcm_state_create(const agcm_grid_t* g, int precision, int nmembers, agcm_st
 int agcm_state_destroy(agcm_state_t* s) {
   if (!s) return AGCM_OK;
   cudaDeviceSynchronize();
+  release_streams(s);
   for (void* p : s->owned) dev_free(p);
   {
     std::lock_guard<std::mutex> lk(g_grid_mu);
@@ -1251,6 +1328,7 @@ int tendency_static(const agcm_grid* g, char* base, const void* U, const void* V
   G.oms = levT + 5 * lS;
   G.rho = levT + 6 * lS;
   G.nl = g->beta2 != 0.0 && g->th.delta != 0.0;
+  leap1_band(g, &G.l1lo, &G.l1hi);  // no second stream here: the two launches run in order
   G.dsd = rawlev + 1 * lS;
   G.shd = rawlev + 0 * lS;
   G.Ad = raw + 3 * rS;

@@ -52,6 +52,7 @@ struct Geom {
   const T* rt0pit;  // R T~_s / pi~
   const T* pit;     // pi~: standard surface pressure / p0 under phi_s
   int nl;           // 1: the delta kappa Phi/P term is on (beta2 != 0)
+  int l1lo, l1hi;   // rows [l1lo, l1hi): interior rows whose strides Mu_j, Mv_j, Mu_{j+1} are all 1
   T rady;           // 1 / (a dth)
 };
 

@@ -23,6 +23,14 @@
 // because P does not depend on k — and every stage accumulates Ubar/Vbar of
 // its own output for the next stage.  One stage therefore reads x_s and x_n
 // and writes x_{s+1}: the 6/9/9 words per grid point of the algorithmic model.
+//
+// A stage is two launches of k_fused_stage, run concurrently on two streams:
+// the low-latitude band of rows whose strides M_j (scalar/U row j and row
+// j+1, V row j) are all 1 — half of the rows under Eq. 7 — with the column
+// body specialised to stride 1 (every leap offset is i or i +- 1, so
+// coinciding loads and P factors are one value and the stencil needs 17
+// instead of 31 loads per level, with no register spills), and the remaining
+// rows with the general body.
 #pragma once
 #include "agcm_common.cuh"
 
@@ -36,6 +44,13 @@ namespace agcm {
 // bound by the FP64 pipe and keeps more registers).
 #ifndef AGCM_FUSED_MINB
 #define AGCM_FUSED_MINB 20
+#endif
+// The stride-1 body needs fewer registers: 28 resident blocks (<= 72
+// registers) measured fastest for it (0.594 ms per stage against 0.600 at 24
+// and 0.627 with the two launches serialised on one stream, 0.653 for the
+// general body over all rows).
+#ifndef AGCM_FUSED_MINB_L1
+#define AGCM_FUSED_MINB_L1 28
 #endif
 #ifndef AGCM_FUSED_MINB64
 #define AGCM_FUSED_MINB64 8
@@ -157,7 +172,7 @@ __device__ __forceinline__ void tile_issue(const TileCtx<T>& t, const Geom<T>& g
 // Omega~ conversion, dpi/dt), 3 = both (the unsplit step).
 // NL: Eq. 1's delta kappa Phi/P term is on; every Phi/P that enters psi or
 // the Omega~ coefficient is scaled by 1 + rho_k Phi/P.
-template <class T, int MODE, bool TILE, int TERMS = 3, bool NL = false>
+template <class T, int MODE, bool TILE, int TERMS = 3, bool NL = false, bool L1 = false>
 __device__ __forceinline__ void fused_column(
     const Geom<T>& g, const int i, const int j, const T* __restrict__ U, const T* __restrict__ V,
     const T* __restrict__ Phi, const T* __restrict__ pi, const double* __restrict__ Ubar,
@@ -166,26 +181,31 @@ __device__ __forceinline__ void fused_column(
     const TileCtx<T>* tc = nullptr, const bool active = true) {
   const int I = g.I, J = g.J, K = g.K;
   constexpr bool ADV = (TERMS & 1) != 0, ADA = (TERMS & 2) != 0;
-  const bool hasS = j < J - 1;   // V row j exists, scalar row j+1 exists
-  const bool hasN = j > 0;       // V row j-1 exists
-  const bool hasSS = j + 1 < J - 1;  // V row j+1 exists
+  const bool hasS = L1 || j < J - 1;   // V row j exists, scalar row j+1 exists
+  const bool hasN = L1 || j > 0;       // V row j-1 exists
+  const bool hasSS = L1 || j + 1 < J - 1;  // V row j+1 exists
   const unsigned plane = (unsigned)J * I, vplane = (unsigned)(J - 1) * I;
   const int rj = j * I, rjm = hasN ? rj - I : rj, rjp = hasS ? rj + I : rj;
 
   // ---- level-independent indices (leap offsets, Eq. 6 / Table "Communication aggregation")
-  const int M = g.Mu[j];
+  // L1: every stride of the stencil is 1 and the row is interior, so the
+  // leap offsets are i and i +- 1; the compiler then merges the loads and P
+  // factors at coinciding points.  The operations are the same; their
+  // contraction into FMAs may differ, so results agree with the general body
+  // to rounding, not to the bit
+  const int M = L1 ? 1 : g.Mu[j];
   const int ip = wrapi(i + 1, I), im = wrapi(i - 1, I);
-  const int ie = wrapi(i + M, I), iw = wrapi(i - M, I);
-  const int fE = wrapi(i + (M - 1) / 2, I), fE1 = wrapi(i + (M + 1) / 2, I);
-  const int fW = wrapi(i - (M + 1) / 2, I), fW1 = wrapi(i - (M - 1) / 2, I);
+  const int ie = L1 ? ip : wrapi(i + M, I), iw = L1 ? im : wrapi(i - M, I);
+  const int fE = L1 ? i : wrapi(i + (M - 1) / 2, I), fE1 = L1 ? ip : wrapi(i + (M + 1) / 2, I);
+  const int fW = L1 ? im : wrapi(i - (M + 1) / 2, I), fW1 = L1 ? i : wrapi(i - (M - 1) / 2, I);
   int Mv = 1, M1 = 1;
-  if (hasS) {
+  if (hasS && !L1) {
     Mv = g.Mv[j];
     M1 = g.Mu[j + 1];
   }
-  const int vie = wrapi(i + Mv, I), viw = wrapi(i - Mv, I);
-  const int vfE = wrapi(i + (Mv - 1) / 2, I), vfW = wrapi(i - (Mv + 1) / 2, I);
-  const int gE = wrapi(i + (M1 - 1) / 2, I), gW = wrapi(i - (M1 + 1) / 2, I);
+  const int vie = L1 ? ip : wrapi(i + Mv, I), viw = L1 ? im : wrapi(i - Mv, I);
+  const int vfE = L1 ? i : wrapi(i + (Mv - 1) / 2, I), vfW = L1 ? im : wrapi(i - (Mv + 1) / 2, I);
+  const int gE = L1 ? i : wrapi(i + (M1 - 1) / 2, I), gW = L1 ? im : wrapi(i - (M1 + 1) / 2, I);
 
   // ---- indices of the level loads: shared-memory tile or global rows
   int lr0 = rj, lrN = rjm, lrS = rjp;
@@ -509,8 +529,8 @@ __device__ __forceinline__ void fused_column(
 // global memory (the row index is warp-uniform, so row tables sit in uniform
 // registers).  BY = kTileY: a 32 x 4 tile whose levels are staged in shared
 // memory by the TMA bulk-copy engine (global loads where the halo is too wide).
-template <class T, int MODE, int BY, int TERMS = 3, bool NL = false>
-__global__ void __launch_bounds__(kTileX* BY, BY == 1 ? (sizeof(T) == 4 ? AGCM_FUSED_MINB : AGCM_FUSED_MINB64)
+template <class T, int MODE, int BY, int TERMS = 3, bool NL = false, int PART = 0>
+__global__ void __launch_bounds__(kTileX* BY, BY == 1 ? (sizeof(T) == 4 ? (PART == 2 ? AGCM_FUSED_MINB_L1 : AGCM_FUSED_MINB) : AGCM_FUSED_MINB64)
                                                       : (sizeof(T) == 4 ? AGCM_TILE_MINB : 2))
     k_fused_stage(Geom<T> g, const T* __restrict__ U, const T* __restrict__ V, const T* __restrict__ Phi,
                   const T* __restrict__ pi, const double* __restrict__ Ubar, const double* __restrict__ Vbar,
@@ -519,10 +539,15 @@ __global__ void __launch_bounds__(kTileX* BY, BY == 1 ? (sizeof(T) == 4 ? AGCM_F
                   int tile_enable, int* err) {
   const int tx = threadIdx.x;
   if (BY == 1) {
-    const int i = blockIdx.x * kTileX + tx, j = blockIdx.y;
+    // PART 0: every row; 1: the rows outside the stride-1 band [l1lo, l1hi);
+    // 2: the band, with the stride-1 column body
+    const int i = blockIdx.x * kTileX + tx;
+    int j = blockIdx.y;
+    if (PART == 1 && j >= g.l1lo) j += g.l1hi - g.l1lo;
+    if (PART == 2) j += g.l1lo;
     if (i < g.I)
-      fused_column<T, MODE, false, TERMS, NL>(g, i, j, U, V, Phi, pi, Ubar, Vbar, Ub, Vb, Phib, pib, Uo, Vo, Phio, pio, Ubar_o,
-                                   Vbar_o, Ubar_b, Vbar_b, cdt);
+      fused_column<T, MODE, false, TERMS, NL, PART == 2>(g, i, j, U, V, Phi, pi, Ubar, Vbar, Ub, Vb, Phib, pib, Uo, Vo,
+                                                         Phio, pio, Ubar_o, Vbar_o, Ubar_b, Vbar_b, cdt);
     return;
   }
   const int ty = threadIdx.y;

@@ -89,10 +89,39 @@ def test_profiler_counts_launches():
     s.filter()
     prof = s.profile_read()
     s.profile(False)
-    assert prof["k_fused_stage"][1] == 15  # three stages per step
+    # three stages per step; a stage is two launches when the grid has both a
+    # band of interior rows whose strides Mu_j, Mv_j, Mu_{j+1} are all 1 and
+    # other rows
+    lu, lv = g.leap()
+    band = [j for j in range(1, J - 2) if lu[j] == 1 and lv[j] == 1 and lu[j + 1] == 1]
+    assert 0 < len(band) < J
+    assert prof["k_fused_stage"][1] == 30
     assert prof["k_vsum"][1] == 1  # exact vertical means once per step call after a load
     assert prof["k_filter"][1] == 1
     assert all(ms > 0 for ms, n in prof.values())
+    s.close()
+
+
+@pytest.mark.parametrize("leap", ["ones", "eq7", "none"])
+def test_stage_launch_count_follows_the_stride1_band(leap):
+    """A stage is two launches when the grid has a run of interior rows
+    whose strides Mu_j, Mv_j, Mu_{j+1} are all 1 and rows outside it, else
+    one; the tendency matches the oracle either way (parity tests)."""
+    I, J, K = (24, 10, 3) if leap != "none" else (5, 3, 2)
+    mu = mv = None
+    if leap != "eq7":
+        mu, mv = np.ones(J, np.int32), np.ones(J - 1, np.int32)
+    g = agcm.Grid(I, J, K, leap_u=mu, leap_v=mv)
+    lu, lv = g.leap()
+    band = [j for j in range(1, J - 2) if lu[j] == 1 and lv[j] == 1 and lu[j + 1] == 1]
+    s = agcm.State(g, agcm.AGCM_FP64)
+    s.load(inputs.random_state(I, J, K, seed=2))
+    s.profile(True)
+    s.step(2, g.dt(100.0))
+    n = s.profile_read()["k_fused_stage"][1]
+    s.profile(False)
+    assert n == 6 * (2 if band else 1), (leap, band, n)
+    assert (leap == "none") == (not band)
     s.close()
 
 

@@ -41,6 +41,11 @@ CASES = [
     (5, 3, 1, "random", {"ones": True}),  # Eq. 7 would ask for 2M >= nlon here
     (128, 64, 8, "rh4", {}),
     (256, 128, 30, "jet", {}),
+    # the stride-1 row band (interior rows whose Mu_j, Mv_j, Mu_{j+1} are 1)
+    # runs a specialised column body beside the general one
+    (24, 10, 4, "random", {"ones": True}),  # band = rows 1..J-3, general body for 0, J-2, J-1
+    (24, 4, 3, "random", {"ones": True}),  # a one-row band
+    (30, 14, 5, "random", {"two_runs": True}),  # the shorter stride-1 run takes the general body
 ]
 
 
@@ -58,6 +63,10 @@ def make_case(nlon, nlat, nlev, kind, extra, seed=11):
         mv = 2 * rng.integers(0, (nlon - 1) // 4 + 1, nlat - 1) + 1
     if extra.get("ones"):
         mu, mv = np.ones(nlat, np.int32), np.ones(nlat - 1, np.int32)
+    if extra.get("two_runs"):  # stride-1 runs at rows 1-2 and 6-10
+        mu = np.array([3, 1, 1, 1, 3, 3, 1, 1, 1, 1, 1, 1, 3, 3], np.int32)
+        mv = np.ones(nlat - 1, np.int32)
+        mv[4] = 3
     sig = extra.get("sigma_half")
     g = agcm.Grid(nlon, nlat, nlev, sigma_half=sig, leap_u=mu, leap_v=mv, phis=st["phis"])
     o = oracle.Oracle(nlon, nlat, nlev, sigma_half=sig, leap_u=mu, leap_v=mv, phis=st["phis"])

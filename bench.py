@@ -43,7 +43,7 @@ BYTES_PER_POINT_STEP = {4: 96, 8: 192}  # 24 words: stages read/write 6 + 9 + 9 
 NCU_TRAFFIC = {
     # kernel name: (sha1 of csrc/agcm_fused.cuh at capture time, bytes per stage
     # summed over the stage's launches, profile file)
-    "k_fused_stage": ("dfd644161e5064f99b3e443a75adeb3c89866f06", 1061100203,
+    "k_fused_stage": ("a158a453d601b41695444c2c22bff95e79ec9cf7", 1060219904,
                       "profiles/fused_stage_1440x720x30_fp32.md"),
 }
 
@@ -53,7 +53,7 @@ NCU_TRAFFIC = {
 # (fadd + fmul + 2 ffma), thread instructions per point, warp instructions
 # issued per point.
 NCU_OPS = {
-    "k_fused_stage": ("dfd644161e5064f99b3e443a75adeb3c89866f06", 218.0, 460.1, 14.70,
+    "k_fused_stage": ("a158a453d601b41695444c2c22bff95e79ec9cf7", 218.0, 460.1, 14.70,
                       "profiles/fused_stage_ops_720x360x30_fp32.md"),
 }
 

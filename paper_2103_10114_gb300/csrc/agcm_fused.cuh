@@ -1,4 +1,4 @@
-// agcm_fused.cuh — the production stage kernel: one launch per stage.
+// agcm_fused.cuh — the production stage kernel: a whole stage in one pass over the levels.
 //
 // One thread owns the column (j, i): the scalar/Phi point (j, i), the U point
 // (j, u = i) and, for j < J-1, the V point (j, i).  It streams the levels from
@@ -40,8 +40,8 @@ namespace agcm {
 // one row (the row index is then warp-uniform, so the row geometry and leap
 // strides live in uniform registers), and a register cap from the number of
 // resident blocks requested (measured on GB300 at 1440x720x30: 20 one-warp
-// blocks per SM, i.e. <= 96 registers, is the fastest FP32 shape; FP64 is
-// bound by the FP64 pipe and keeps more registers).
+// blocks per SM, i.e. <= 96 registers, is the fastest FP32 shape for the
+// general body; FP64 is bound by the FP64 pipe and keeps more registers).
 #ifndef AGCM_FUSED_MINB
 #define AGCM_FUSED_MINB 20
 #endif
@@ -527,8 +527,9 @@ __device__ __forceinline__ void fused_column(
 
 // BY = 1: one warp per block covering 32 columns of one row, loads from
 // global memory (the row index is warp-uniform, so row tables sit in uniform
-// registers).  BY = kTileY: a 32 x 4 tile whose levels are staged in shared
-// memory by the TMA bulk-copy engine (global loads where the halo is too wide).
+// registers); PART picks the rows of the launch.  BY = kTileY: a 32 x 4 tile
+// whose levels are staged in shared memory by the TMA bulk-copy engine (global
+// loads where the halo is too wide).
 template <class T, int MODE, int BY, int TERMS = 3, bool NL = false, int PART = 0>
 __global__ void __launch_bounds__(kTileX* BY, BY == 1 ? (sizeof(T) == 4 ? (PART == 2 ? AGCM_FUSED_MINB_L1 : AGCM_FUSED_MINB) : AGCM_FUSED_MINB64)
                                                       : (sizeof(T) == 4 ? AGCM_TILE_MINB : 2))

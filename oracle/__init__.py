@@ -41,34 +41,39 @@ def build(force: bool = False) -> str:
 _lib = None
 
 
+def bind(cdll):
+    """Declare the oracle's C signatures on a loaded library and return it."""
+    d, i32, vp = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p
+    cdll.orc_leap_ratio.restype = ctypes.c_double
+    cdll.orc_leap_ratio.argtypes = [ctypes.c_double, ctypes.c_double]
+    cdll.orc_zonal_dx.restype = ctypes.c_double
+    cdll.orc_zonal_dx.argtypes = [ctypes.c_double, ctypes.c_double]
+    cdll.orc_leap_table.argtypes = [ctypes.c_int, ctypes.c_int, i32, i32]
+    cdll.orc_create.restype = vp
+    cdll.orc_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, d, i32, i32, d]
+    cdll.orc_destroy.argtypes = [vp]
+    cdll.orc_get_leap.argtypes = [vp, i32, i32]
+    cdll.orc_tendency.argtypes = [vp] + [d] * 8 + [ctypes.c_uint]
+    cdll.orc_step.argtypes = [vp] + [d] * 4 + [ctypes.c_double, ctypes.c_int, ctypes.c_uint]
+    cdll.orc_tendency_jvp.argtypes = [vp] + [d] * 12 + [ctypes.c_uint]
+    cdll.orc_step_jvp.argtypes = [vp] + [d] * 8 + [ctypes.c_double, ctypes.c_int, ctypes.c_uint]
+    cdll.orc_diagnostics.argtypes = [vp] + [d] * 5
+    cdll.orc_filter_band.restype = ctypes.c_int
+    cdll.orc_filter_band.argtypes = [ctypes.c_double]
+    cdll.orc_filter.argtypes = [vp] + [d] * 4 + [ctypes.c_double]
+    cdll.orc_set_thermo.restype = ctypes.c_int
+    cdll.orc_set_thermo.argtypes = [vp, d]
+    cdll.orc_std_temp.restype = ctypes.c_double
+    cdll.orc_std_temp.argtypes = [d, ctypes.c_double]
+    cdll.orc_std_surface.argtypes = [d, ctypes.c_double, d]
+    cdll.orc_tendency_opcount.argtypes = [vp] + [d] * 8 + [ctypes.c_uint, ctypes.POINTER(ctypes.c_ulonglong)]
+    return cdll
+
+
 def lib():
     global _lib
     if _lib is None:
-        _lib = ctypes.CDLL(build())
-        d, i32, vp = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p
-        _lib.orc_leap_ratio.restype = ctypes.c_double
-        _lib.orc_leap_ratio.argtypes = [ctypes.c_double, ctypes.c_double]
-        _lib.orc_zonal_dx.restype = ctypes.c_double
-        _lib.orc_zonal_dx.argtypes = [ctypes.c_double, ctypes.c_double]
-        _lib.orc_leap_table.argtypes = [ctypes.c_int, ctypes.c_int, i32, i32]
-        _lib.orc_create.restype = vp
-        _lib.orc_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, d, i32, i32, d]
-        _lib.orc_destroy.argtypes = [vp]
-        _lib.orc_get_leap.argtypes = [vp, i32, i32]
-        _lib.orc_tendency.argtypes = [vp] + [d] * 8 + [ctypes.c_uint]
-        _lib.orc_step.argtypes = [vp] + [d] * 4 + [ctypes.c_double, ctypes.c_int, ctypes.c_uint]
-        _lib.orc_tendency_jvp.argtypes = [vp] + [d] * 12 + [ctypes.c_uint]
-        _lib.orc_step_jvp.argtypes = [vp] + [d] * 8 + [ctypes.c_double, ctypes.c_int, ctypes.c_uint]
-        _lib.orc_diagnostics.argtypes = [vp] + [d] * 5
-        _lib.orc_filter_band.restype = ctypes.c_int
-        _lib.orc_filter_band.argtypes = [ctypes.c_double]
-        _lib.orc_filter.argtypes = [vp] + [d] * 4 + [ctypes.c_double]
-        _lib.orc_set_thermo.restype = ctypes.c_int
-        _lib.orc_set_thermo.argtypes = [vp, d]
-        _lib.orc_std_temp.restype = ctypes.c_double
-        _lib.orc_std_temp.argtypes = [d, ctypes.c_double]
-        _lib.orc_std_surface.argtypes = [d, ctypes.c_double, d]
-        _lib.orc_tendency_opcount.argtypes = [vp] + [d] * 8 + [ctypes.c_uint, ctypes.POINTER(ctypes.c_ulonglong)]
+        _lib = bind(ctypes.CDLL(build()))
     return _lib
 
 
@@ -153,7 +158,7 @@ class Oracle:
         mu = opt(leap_u, np.int32, self.J)
         mv = opt(leap_v, np.int32, self.J - 1)
         ph = opt(phis, np.float64, self.J * self.I)
-        L = lib()
+        self._L = L = lib()
         self._h = L.orc_create(
             self.I, self.J, self.K,
             _dp(sh) if sh is not None else None,
@@ -175,7 +180,7 @@ class Oracle:
     def __del__(self):
         h = getattr(self, "_h", None)
         if h:
-            lib().orc_destroy(h)
+            self._L.orc_destroy(h)
             self._h = None
 
     # -- shapes ----------------------------------------------------------
@@ -194,7 +199,7 @@ class Oracle:
     def tendency(self, st, terms=TERM_ALL):
         x = self._in(st)
         t = self.zeros()
-        lib().orc_tendency(self._h, *[_dp(a) for a in x], *[_dp(t[f]) for f in FIELDS], terms)
+        self._L.orc_tendency(self._h, *[_dp(a) for a in x], *[_dp(t[f]) for f in FIELDS], terms)
         return t
 
     def tendency_opcount(self, st, terms=TERM_ALL):
@@ -204,18 +209,18 @@ class Oracle:
         x = self._in(st)
         t = self.zeros()
         ops = (ctypes.c_ulonglong * 4)()
-        lib().orc_tendency_opcount(self._h, *[_dp(a) for a in x], *[_dp(t[f]) for f in FIELDS], terms, ops)
+        self._L.orc_tendency_opcount(self._h, *[_dp(a) for a in x], *[_dp(t[f]) for f in FIELDS], terms, ops)
         return t, dict(zip(("add", "mul", "div", "sqrt"), [int(v) for v in ops]))
 
     def step(self, st, dt, nsteps=1, terms=TERM_ALL):
         x = [a.copy() for a in self._in(st)]
-        lib().orc_step(self._h, *[_dp(a) for a in x], float(dt), int(nsteps), terms)
+        self._L.orc_step(self._h, *[_dp(a) for a in x], float(dt), int(nsteps), terms)
         return dict(zip(FIELDS, x))
 
     def tendency_jvp(self, st, dst, terms=TERM_ALL):
         x, dx = self._in(st), self._in(dst)
         j = self.zeros()
-        lib().orc_tendency_jvp(self._h, *[_dp(a) for a in x], *[_dp(a) for a in dx],
+        self._L.orc_tendency_jvp(self._h, *[_dp(a) for a in x], *[_dp(a) for a in dx],
                                *[_dp(j[f]) for f in FIELDS], terms)
         return j
 
@@ -223,19 +228,19 @@ class Oracle:
         """Returns (state after nsteps, Jacobian of the nsteps map applied to dst)."""
         x = [a.copy() for a in self._in(st)]
         dx = [a.copy() for a in self._in(dst)]
-        lib().orc_step_jvp(self._h, *[_dp(a) for a in x], *[_dp(a) for a in dx], float(dt),
+        self._L.orc_step_jvp(self._h, *[_dp(a) for a in x], *[_dp(a) for a in dx], float(dt),
                            int(nsteps), terms)
         return dict(zip(FIELDS, x)), dict(zip(FIELDS, dx))
 
     def filter(self, st, r=0.25):
         """Low-latitude filters (Table "Conventional Filtering scheme"), a new state."""
         x = [a.copy() for a in self._in(st)]
-        lib().orc_filter(self._h, *[_dp(a) for a in x], float(r))
+        self._L.orc_filter(self._h, *[_dp(a) for a in x], float(r))
         return dict(zip(FIELDS, x))
 
     def diagnostics(self, st):
         x = self._in(st)
         out = np.zeros(8)
-        lib().orc_diagnostics(self._h, *[_dp(a) for a in x], _dp(out))
+        self._L.orc_diagnostics(self._h, *[_dp(a) for a in x], _dp(out))
         keys = ("mass", "e_kin", "e_pot", "e_ps", "energy", "max_u", "max_v", "finite")
         return dict(zip(keys, out.tolist()))

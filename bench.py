@@ -38,13 +38,12 @@ sys.path.insert(0, ROOT)
 WORKLOAD = (1440, 720, 30)
 BYTES_PER_POINT_STEP = {4: 96, 8: 192}  # 24 words: stages read/write 6 + 9 + 9 words
 
-# DRAM traffic of the dominant kernel from an ncu capture of this workload
-# (profiles/), valid only while the kernel source is the one that was captured.
+# DRAM traffic of the dominant kernel from an ncu capture of this workload,
+# valid only while the kernel source is the one that was captured.
 NCU_TRAFFIC = {
     # kernel name: (sha1 of csrc/agcm_fused.cuh at capture time, bytes per stage
-    # summed over the stage's launches, profile file)
-    "k_fused_stage": ("a158a453d601b41695444c2c22bff95e79ec9cf7", 1060219904,
-                      "profiles/fused_stage_1440x720x30_fp32.md"),
+    # summed over the stage's launches)
+    "k_fused_stage": ("a158a453d601b41695444c2c22bff95e79ec9cf7", 1060219904),
 }
 
 # Instruction counters of the dominant kernel (ncu, 720x360x30 FP32, the launches
@@ -53,8 +52,7 @@ NCU_TRAFFIC = {
 # (fadd + fmul + 2 ffma), thread instructions per point, warp instructions
 # issued per point.
 NCU_OPS = {
-    "k_fused_stage": ("a158a453d601b41695444c2c22bff95e79ec9cf7", 218.0, 460.1, 14.70,
-                      "profiles/fused_stage_ops_720x360x30_fp32.md"),
+    "k_fused_stage": ("a158a453d601b41695444c2c22bff95e79ec9cf7", 218.0, 460.1, 14.70),
 }
 
 
@@ -277,6 +275,7 @@ def main():
     # warm-up
     s.step(args.warmup, dt)
     torch.cuda.synchronize()
+    d0 = s.diagnostics()  # conservation reference at the start of the timed steps
     # timed region: device-resident inputs
     s.profile(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -331,7 +330,7 @@ def main():
     traffic, traffic_src = None, None
     rec = NCU_TRAFFIC.get(name)
     if rec and rec[0] == kernel_source_hash():
-        traffic, traffic_src = rec[1], rec[2]
+        traffic, traffic_src = rec[1], f"ncu dram read + write per stage, source sha1 {rec[0][:12]}"
     compute = None
     orec = NCU_OPS.get(name)
     if orec and orec[0] == kernel_source_hash():
@@ -347,7 +346,7 @@ def main():
                    "fp32_tflops": fp32, "fp32_peak_tflops": fp32_peak, "fp32_frac": fp32 / fp32_peak,
                    "warp_inst_per_point_stage": orec[3], "issue_frac": issue / issue_peak,
                    "peak_note": f"{nsm} SMs x 128 FP32 lanes x 2 x {fmax:.0f} MHz; issue: 4 warp-inst/SM/cycle",
-                   "source": orec[4]}
+                   "source": f"ncu instruction counters, 720x360x30 FP32, source sha1 {orec[0][:12]}"}
     launches = sum(n for _, n in prof.values())
     line = {
         "metric": "grid-point-steps/s", "value": value, "unit": "gp-steps/s", "n_gpus": world,
@@ -372,7 +371,12 @@ def main():
         "gpu_launches": launches,
         "clocks": clocks,
         "sypd_equiv": (value / world / pts) * dt / 365.0,
-        "energy_ok": bool(d["finite"]),
+        "finite": bool(d["finite"]),
+        # relative change over the timed steps, from the FP64 diagnostics (mass:
+        # area sum of the surface pressure; energy: the total effective energy)
+        "drift": {"mass": (d["mass"] - d0["mass"]) / d0["mass"],
+                  "energy": (d["energy"] - d0["energy"]) / d0["energy"], "steps": args.steps,
+                  "simulated_hours": args.steps * dt / 3600.0},
     }
     if rank == 0 and not args.no_forms:
         line["forms"] = measure_forms(agcm, inputs, torch)

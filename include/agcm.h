@@ -146,10 +146,13 @@ int agcm_state_create(const agcm_grid_t* grid, int precision, int nmembers, agcm
 int agcm_state_destroy(agcm_state_t* state);
 
 /*
- * Load or store the prognostic fields.  Pointers hold the state's element
- * type in the layout above; on_device = 1 for device pointers, 0 for host
- * pointers (pinned host memory gives asynchronous copies).  Asynchronous on
- * `stream`.
+ * Load or store the prognostic fields: the forecast variables of Eq. 1 after
+ * the IAP transform and the subtraction of the standard stratification
+ * (Sec. "Governing equations": U, V, Phi and p'_sa / p0; Eq. 2's F), here
+ * U and V (the IAP wind P u, P v), Phi and pi = p'_sa / p0.  Pointers hold
+ * the state's element type in the layout above; on_device = 1 for device
+ * pointers, 0 for host pointers (pinned host memory gives asynchronous
+ * copies).  Asynchronous on `stream`.
  */
 int agcm_state_load(agcm_state_t* state, const void* U, const void* V, const void* Phi,
                     const void* pi, int on_device, void* stream);
@@ -211,7 +214,13 @@ int agcm_tendency(agcm_state_t* state, void* tU, void* tV, void* tPhi, void* tpi
 int agcm_step_adjoint(agcm_state_t* xn, const void* const lam_in[4], void* const lam_out[4], double dt,
                       void* stream);
 
-/* Diagnostics (a11): FP64 global sums and maxima.  Synchronises `stream`. */
+/*
+ * Diagnostics: FP64 global sums and maxima of x_n.  The energy is the total
+ * effective energy of Sec. "Validation" (the energy-conservation figure):
+ * kinetic plus available potential plus available surface potential energy,
+ * in the IAP variables, whose sum the spatial operator conserves exactly;
+ * mass is the area sum of the surface pressure.  Synchronises `stream`.
+ */
 typedef struct agcm_diag {
   double mass;      /* sum_j A_j (pi~ + pi)  [p0 m^2] */
   double e_kin;     /* 1/2 sum dsigma (A U^2 + Av V^2) */
@@ -279,21 +288,24 @@ int agcm_ensemble_profile(agcm_ensemble_t* ens, int enable, double* ms_total, in
 
 /*
  * agcm_tendency_static — T(x) like agcm_tendency, for callers that cannot
- * allocate device memory (a caller inside a CUDA-graph capture or under a
- * memory budget that forbids new allocations, or an embedder whose allocator
- * owns all device memory and lends the library only its buffers).  The paper
- * has no counterpart; this is a deployment convenience.
+ * allocate device memory: an application running under a fixed device-memory
+ * budget that forbids new allocations, or an embedder whose allocator owns
+ * all device memory and lends the library only its buffers.  The paper has no
+ * counterpart; this is a deployment convenience.
  *   grid:   created with agcm_grid_create (host only); nlon*nlat <= 262144,
  *           nlat <= 4096, nlev <= 256 — larger grids return AGCM_EINVAL.
  *   U, V, Phi, pi: caller-owned device input (layout above, element type of
  *           `precision`); tU, tV, tPhi, tpi: caller-owned device output.
  * The call allocates nothing: its scratch (the grid's device tables and the
  * FP64 vertical means, about 13 MB) is one fixed array that every GPU holds
- * from library load until process exit.  Every call overwrites that array, so
- * calls whose kernels overlap on a GPU (other streams, other threads) race;
- * serialise them.  The first call on a device looks up the array's device
- * address (set-up, once per device, with that device current); make that
- * first call before any stream capture.  Asynchronous on `stream`.
+ * from library load until process exit.  Every call overwrites the vertical
+ * means in that array, and a call on another grid (or precision) rebuilds the
+ * tables in it (a call on the grid of the previous call on that device
+ * reuses them), so calls whose kernels overlap on a GPU (other streams,
+ * other threads) race; serialise them.  The first call on a device looks up
+ * the array's device address (set-up, once per device, with that device
+ * current); make that first call before any stream capture.  Asynchronous on
+ * `stream`.
  */
 int agcm_tendency_static(const agcm_grid_t* grid, int precision, const void* U, const void* V, const void* Phi,
                          const void* pi, void* tU, void* tV, void* tPhi, void* tpi, void* stream);

@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -48,6 +49,8 @@ int fail(int code, const char* fmt, ...) {
     cudaError_t e_ = (expr);                                                        \
     if (e_ != cudaSuccess) return fail(AGCM_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
   } while (0)
+
+std::atomic<uint64_t> g_grid_uid{0};
 
 // Guards every grid's lazily built device tables and its count of live
 // states and ensembles, so that states may be created and destroyed from
@@ -108,6 +111,10 @@ struct DevGeomBlob {
 
 struct agcm_grid {
   int I = 0, J = 0, K = 0;
+  // process-unique id of the grid's tables, renewed when they change
+  // (agcm_grid_set_thermo): the allocation-free tendency keeps the last
+  // grid's device tables and rebuilds them only when this id changes
+  uint64_t uid = 0;
   double dlam = 0, dth = 0;
   std::vector<double> s, c, cot, A, sv, Av, sh, ds, Hkk, hk, pit;
   // thermodynamics (agcm_grid_set_thermo): surface geopotential, the level
@@ -454,13 +461,6 @@ int ensure_bar(agcm_state* s, cudaStream_t st) {
 // One fused stage: out = base + cdt * T(x[in]) (MODE 1: base = x[in]; MODE 2:
 // base = x[0]; MODE 0: out = T).  Writes the vertical means of out to bar[outb]
 // (outb < 0: not written).
-// Launch of the stage kernel.  AGCM_STAGE_TILE selects the shape: 0 = one
-// warp per 32-column row segment with global loads (default: fastest on GB300
-// at 1440x720x30: 0.59 ms per stage against 0.96 ms for the tiles), 1 = 32 x 4
-// tiles staged by TMA.
-#ifndef AGCM_STAGE_TILE
-#define AGCM_STAGE_TILE 0
-#endif
 // Rows launch: the stride-1 band [l1lo, l1hi) with the specialised column
 // body and the other rows with the general one.  Given aux, evf and evj (a
 // second stream and two events), the band runs on aux, forked from st after
@@ -479,11 +479,11 @@ int launch_fused(const agcm::Geom<T>& G, const void* const xs[4], const double* 
     const unsigned gx = (unsigned)((G.I + agcm::kTileX - 1) / agcm::kTileX);
     const int nb = G.l1hi - G.l1lo;
     auto go = [&](auto part, int ny, cudaStream_t q) {
-      agcm::k_fused_stage<T, MODE, 1, TERMS, decltype(nl)::value, decltype(part)::value>
+      agcm::k_fused_stage<T, MODE, TERMS, decltype(nl)::value, decltype(part)::value>
           <<<dim3(gx, (unsigned)ny), block, 0, q>>>(
               G, (const T*)xs[0], (const T*)xs[1], (const T*)xs[2], (const T*)xs[3], ub, vb, (const T*)xb[0],
               (const T*)xb[1], (const T*)xb[2], (const T*)xb[3], (T*)out[0], (T*)out[1], (T*)out[2], (T*)out[3],
-              ubo, vbo, ubb, vbb, (T)cdt, 0, err);
+              ubo, vbo, ubb, vbb, (T)cdt);
     };
     if (nb <= 0) {
       go(std::integral_constant<int, 0>{}, G.J, st);
@@ -510,30 +510,7 @@ int launch_fused(const agcm::Geom<T>& G, const void* const xs[4], const double* 
   if constexpr ((TERMS & 2) != 0) {
     if (G.nl) return rows(std::true_type{});
   }
-  if constexpr (!AGCM_STAGE_TILE || TERMS != 3) {
-    return rows(std::false_type{});
-  } else {
-  static bool attr_set = false;  // per process; the attribute is per function
-  const size_t smem = agcm::tile_smem_bytes<T>();
-  if (!attr_set) {
-    CUDA_TRY(cudaFuncSetAttribute(agcm::k_fused_stage<T, MODE, agcm::kTileY>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr_set = true;
-  }
-  // the bulk copies need 16-byte aligned row segments of the stage input
-  int tile = 1;
-  for (int f = 0; f < 3; ++f)
-    if (((uintptr_t)xs[f]) & 15) tile = 0;
-  const dim3 block(agcm::kTileX, agcm::kTileY);
-  const dim3 grid((unsigned)((G.I + agcm::kTileX - 1) / agcm::kTileX),
-                  (unsigned)((G.J + agcm::kTileY - 1) / agcm::kTileY));
-  agcm::k_fused_stage<T, MODE, agcm::kTileY><<<grid, block, smem, st>>>(
-      G, (const T*)xs[0], (const T*)xs[1], (const T*)xs[2], (const T*)xs[3], ub, vb, (const T*)xb[0],
-      (const T*)xb[1], (const T*)xb[2], (const T*)xb[3], (T*)out[0], (T*)out[1], (T*)out[2], (T*)out[3], ubo, vbo,
-      ubb, vbb, (T)cdt, tile, err);
-  CUDA_TRY(cudaGetLastError());
-  return AGCM_OK;
-  }
+  return rows(std::false_type{});
 }
 
 template <class T, int MODE, int TERMS = 3>
@@ -692,6 +669,7 @@ int agcm_grid_set_thermo(agcm_grid_t* g, const agcm_thermo_t* t) {
     return fail(AGCM_EINVAL, "agcm_grid_set_thermo: value out of range");
   g->th = v;
   thermo_tables(g);
+  g->uid = ++g_grid_uid;
   return AGCM_OK;
 }
 
@@ -766,6 +744,7 @@ int agcm_grid_create(int nlon, int nlat, int nlev, const double* sigma_half, con
     g->phis[n] = p;
   }
   thermo_tables(g);  // the default isothermal 250 K atmosphere
+  g->uid = ++g_grid_uid;
   *out = g;
   return AGCM_OK;
 }
@@ -1205,9 +1184,9 @@ int adjoint_step(agcm_state* s, const void* const lam_in[4], void* const lam_out
 // tables and the FP64 vertical means Ubar/Vbar) lives in one file-scope
 // __device__ array of fixed size that every GPU holds from the moment this
 // library is loaded until the process exits.  It serves callers that cannot
-// call cudaMalloc: code running inside a CUDA graph capture or a memory-pool
-// budget that forbids new allocations, and embedders whose allocator owns all
-// device memory and hands the library only input and output buffers.
+// call cudaMalloc: an application running under a fixed device-memory budget
+// that forbids new allocations, and embedders whose allocator owns all device
+// memory and hands the library only input and output buffers.
 namespace {
 
 constexpr size_t kStaticCols = 262144;  // nlat * nlon at most (e.g. 720 x 360)
@@ -1237,6 +1216,9 @@ namespace {
 
 std::mutex g_static_mu;
 void* g_static_ptr[kStaticMaxDevices] = {};
+// per device: the grid id and precision whose tables the array holds (0: none)
+uint64_t g_static_uid[kStaticMaxDevices] = {};
+int g_static_prec[kStaticMaxDevices] = {};
 
 // Typed device tables from the raw FP64 ones (same formulas as the state path).
 template <class T>
@@ -1254,7 +1236,10 @@ __global__ void k_static_geom(int I, int J, int K, const double* raw, const doub
   const double* beta = rawlev + 4 * levStride;
   const double dlam = 2.0 * kPi / I, dth = kPi / J;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x; n < (size_t)I * J; n += stride) {
+  // one pass covers the columns, the rows and the levels, whichever is longest
+  // (a grid may have more levels than columns)
+  const size_t ncol = (size_t)I * J, nall = ncol > (size_t)K ? ncol : (size_t)K;
+  for (size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x; n < nall; n += stride) {
     if (n < (size_t)J) {
       const int j = (int)n;
       rowT[0 * rowStride + j] = (T)(1.0 / (kA * s[j] * Mu[j] * dlam));
@@ -1282,14 +1267,18 @@ __global__ void k_static_geom(int I, int J, int K, const double* raw, const doub
       levT[5 * levStride + k] = (T)(1.0 - rawlev[k]);
       levT[6 * levStride + k] = (T)(beta[k] != 0.0 ? beta2 / beta[k] : 0.0);
     }
-    colT[n] = (T)pitraw[n];
-    colT[colStride + n] = (T)(pitraw[colStride + n] / pitraw[n]);
+    if (n < ncol) {
+      colT[n] = (T)pitraw[n];
+      colT[colStride + n] = (T)(pitraw[colStride + n] / pitraw[n]);
+    }
   }
 }
 
+// tables: upload the grid's tables and build the typed ones (false when the
+// array already holds this grid's tables in this precision).
 template <class T>
-int tendency_static(const agcm_grid* g, char* base, const void* U, const void* V, const void* Phi, const void* pi,
-                    void* tU, void* tV, void* tPhi, void* tpi, cudaStream_t st) {
+int tendency_static(const agcm_grid* g, char* base, bool tables, const void* U, const void* V, const void* Phi,
+                    const void* pi, void* tU, void* tV, void* tPhi, void* tpi, cudaStream_t st) {
   const int I = g->I, J = g->J, K = g->K;
   const size_t rS = kRowB / 8, lS = kLevB / 8, cS = kColB / 8;  // strides in elements of 8 bytes
   double* raw = (double*)(base + kOffRaw);
@@ -1297,6 +1286,12 @@ int tendency_static(const agcm_grid* g, char* base, const void* U, const void* V
   double* pitraw = (double*)(base + kOffPitRaw);
   int* Mu = (int*)(base + kOffInt);
   int* Mv = (int*)(base + kOffInt + kRowB);
+  // typed tables are indexed with the element strides rS/lS/cS of the raw
+  // (8-byte) tables, so a float table uses the first half of its region
+  T* rowT = (T*)(base + kOffRowT);
+  T* levT = (T*)(base + kOffLevT);
+  T* colT = (T*)(base + kOffColT);
+  if (tables) {
   const std::vector<double>* rows[6] = {&g->s, &g->c, &g->cot, &g->A, &g->sv, &g->Av};
   for (int q = 0; q < 6; ++q)
     if (!rows[q]->empty())
@@ -1309,13 +1304,10 @@ int tendency_static(const agcm_grid* g, char* base, const void* U, const void* V
   CUDA_TRY(cudaMemcpyAsync(Mu, g->Mu.data(), g->Mu.size() * sizeof(int), cudaMemcpyHostToDevice, st));
   if (!g->Mv.empty())
     CUDA_TRY(cudaMemcpyAsync(Mv, g->Mv.data(), g->Mv.size() * sizeof(int), cudaMemcpyHostToDevice, st));
-  // typed tables are indexed with the element strides rS/lS/cS of the raw
-  // (8-byte) tables, so a float table uses the first half of its region
-  T* rowT = (T*)(base + kOffRowT);
-  T* levT = (T*)(base + kOffLevT);
-  T* colT = (T*)(base + kOffColT);
-  k_static_geom<T><<<nblocks((size_t)I * J, 256), 256, 0, st>>>(I, J, K, raw, rawlev, pitraw, Mu, Mv, rowT, levT,
-                                                                colT, rS, lS, cS, g->beta2);
+  k_static_geom<T><<<nblocks(std::max<size_t>((size_t)I * J, (size_t)K), 256), 256, 0, st>>>(
+      I, J, K, raw, rawlev, pitraw, Mu, Mv, rowT, levT, colT, rS, lS, cS, g->beta2);
+  CUDA_TRY(cudaGetLastError());
+  }
   agcm::Geom<T> G{};
   G.I = I; G.J = J; G.K = K;
   G.Mu = Mu;
@@ -1362,22 +1354,31 @@ extern "C" int agcm_tendency_static(const agcm_grid_t* g, int precision, const v
   CUDA_TRY(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kStaticMaxDevices) return fail(AGCM_EINVAL, "device ordinal %d not supported", dev);
   void* base = nullptr;
-  {
-    std::lock_guard<std::mutex> lk(g_static_mu);
-    if (!g_static_ptr[dev]) {
-      // once per device, with that device current: the device address of the
-      // scratch array (its host-side name is only a stand-in)
-      void* p = nullptr;
-      cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-      if (e != cudaSuccess || !p)
-        return fail(AGCM_ECUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
-      g_static_ptr[dev] = p;
-    }
-    base = g_static_ptr[dev];
+  bool tables = true;
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    // once per device, with that device current: the device address of the
+    // scratch array (its host-side name is only a stand-in)
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(AGCM_ECUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
+    g_static_ptr[dev] = p;
   }
+  base = g_static_ptr[dev];
+  // the array keeps the last call's tables: rebuild them only for another
+  // grid (or the same grid after agcm_grid_set_thermo) or precision
+  tables = g_static_uid[dev] != g->uid || g_static_prec[dev] != precision;
+  g_static_uid[dev] = 0;  // stays 0 if this call fails part-way
   cudaStream_t st = as_stream(stream);
-  return precision == AGCM_FP64 ? tendency_static<double>(g, (char*)base, U, V, Phi, pi, tU, tV, tPhi, tpi, st)
-                                : tendency_static<float>(g, (char*)base, U, V, Phi, pi, tU, tV, tPhi, tpi, st);
+  const int rc = precision == AGCM_FP64
+                     ? tendency_static<double>(g, (char*)base, tables, U, V, Phi, pi, tU, tV, tPhi, tpi, st)
+                     : tendency_static<float>(g, (char*)base, tables, U, V, Phi, pi, tU, tV, tPhi, tpi, st);
+  if (rc == AGCM_OK) {
+    g_static_uid[dev] = g->uid;
+    g_static_prec[dev] = precision;
+  }
+  return rc;
 }
 
 // ================================================================ ensembles

@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(32, sizeof(T) == 4 ? AGCM_ENS_MINB : 8)
             // as base instead of reusing its own values: the same arithmetic)
             const int a = stage, b = stage == 0 ? 1 : (stage == 1 ? 2 : 0);
             const T c = stage == 2 ? e.dt : T(0.5) * e.dt;
-            fused_column<T, 2, false>(g, i, j, e.x[a][0], e.x[a][1], e.x[a][2], e.x[a][3], e.ubar[a], e.vbar[a],
+            fused_column<T, 2>(g, i, j, e.x[a][0], e.x[a][1], e.x[a][2], e.x[a][3], e.ubar[a], e.vbar[a],
                                       e.x[0][0], e.x[0][1], e.x[0][2], e.x[0][3], e.x[b][0], e.x[b][1],
                                       e.x[b][2], e.x[b][3], e.ubar[b], e.vbar[b], e.ubar[0], e.vbar[0], c);
           }

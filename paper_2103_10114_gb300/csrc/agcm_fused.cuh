@@ -55,115 +55,11 @@ namespace agcm {
 #ifndef AGCM_FUSED_MINB64
 #define AGCM_FUSED_MINB64 8
 #endif
-// ---- shared-memory tile staged by the TMA bulk-copy engine
-constexpr int kTileX = 32, kTileY = 4;          // one block = 32 columns x 4 rows
-constexpr int kHaloMax = 64;                    // leap strides up to 63 are staged
-constexpr int kPitch = kTileX + 2 * kHaloMax;   // row pitch of a staged segment
-constexpr int kTileRows = kTileY + 2;           // rows j0-1 .. j0+4
-constexpr int kStages = 3;                      // levels in flight
-#ifndef AGCM_TILE_MINB
-#define AGCM_TILE_MINB 5
-#endif
-template <class T>
-constexpr size_t tile_smem_bytes() {
-  return 64 + sizeof(T) * (size_t)kStages * 3 * kTileRows * kPitch;
-}
-
-__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait: gives up after about a second, records AGCM_ETIMEOUT (4).
-// Once a wait has given up (err set), later waits return at once, so a fault
-// costs one timeout, not one per level.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int* err) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
-    if (err && *(volatile int*)err != 0) return false;
-    if (clock64() - t0 > 2000000000LL) {
-      if (err) atomicExch(err, 4);
-      return false;
-    }
-  }
-  return true;
-}
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-// TMA bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16)
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_u32(dst)),
-               "l"(src), "r"(bytes), "r"(smem_u32(bar))
-               : "memory");
-}
-
-template <class T>
-struct TileCtx {
-  T* buf;           // kStages x 3 fields x kTileRows x kPitch
-  uint64_t* bar;    // kStages mbarriers
-  int H, i0, j0, tx, ty, tid;
-  unsigned tx_bytes;  // bytes one level brings in
-  int* err;
-};
-
-// Issue the copies of level k into stage slot `slot`: per field and staged row
-// one segment of W = 32 + 2H columns starting at i0 - H, split at the seam.
-template <class T>
-__device__ __forceinline__ void tile_issue(const TileCtx<T>& t, const Geom<T>& g, const T* U, const T* Phi,
-                                           const T* V, int k, int slot) {
-  const int I = g.I, J = g.J, W = kTileX + 2 * t.H, c0 = t.i0 - t.H;
-  uint64_t* bar = t.bar + slot;
-  if (t.err && *(volatile int*)t.err != 0) return;  // a wait already gave up: issue nothing more
-  if (t.tid == 0) mbar_arrive_expect_tx(bar, t.tx_bytes);
-  if (t.tid < 36) {
-    const int f = t.tid / 12, r = (t.tid % 12) >> 1, part = t.tid & 1;
-    const int row = t.j0 - 1 + r;
-    const int nrows = f == 2 ? J - 1 : J;
-    if (row >= 0 && row < nrows) {
-      const T* src = (f == 0 ? U : (f == 1 ? Phi : V)) + ((size_t)k * nrows + row) * I;
-      T* dst = t.buf + ((size_t)(slot * 3 + f) * kTileRows + r) * kPitch;
-      int a = 0, len = 0, off = 0;
-      if (part == 0) {
-        a = c0 > 0 ? c0 : 0;
-        const int e = c0 + W < I ? c0 + W : I;
-        len = e - a;
-        off = a - c0;
-      } else if (c0 < 0) {
-        a = I + c0;
-        len = -c0;
-        off = 0;
-      } else if (c0 + W > I) {
-        a = 0;
-        len = c0 + W - I;
-        off = I - c0;
-      }
-      if (len > 0) {
-        fence_proxy_async();
-        bulk_g2s(dst + off, src + a, (unsigned)(len * sizeof(T)), bar);
-      }
-    }
-  }
-}
+constexpr int kTileX = 32;  // columns of one warp (one block) of the stage kernel
 
 // The work of one thread: the column (j, i) through all levels of one stage.
 // MODE 0: out = T(xs) (validation); MODE 1: base = xs (first stage);
 // MODE 2: base given (later stages; may alias out).
-// TILE: the level loads come from the shared-memory tile (all threads of the
-// block must call it, inactive ones with clamped indices and active = false);
-// otherwise from global memory.
 // Ubar_b/Vbar_b: vertical means of the base state (FP32 path, MODE > 0): the
 // output's means are base + sum_k dsigma_k (out_k - base_k), the increments
 // being exact differences of stored floats, so no FP64 work runs per level.
@@ -172,13 +68,12 @@ __device__ __forceinline__ void tile_issue(const TileCtx<T>& t, const Geom<T>& g
 // Omega~ conversion, dpi/dt), 3 = both (the unsplit step).
 // NL: Eq. 1's delta kappa Phi/P term is on; every Phi/P that enters psi or
 // the Omega~ coefficient is scaled by 1 + rho_k Phi/P.
-template <class T, int MODE, bool TILE, int TERMS = 3, bool NL = false, bool L1 = false>
+template <class T, int MODE, int TERMS = 3, bool NL = false, bool L1 = false>
 __device__ __forceinline__ void fused_column(
     const Geom<T>& g, const int i, const int j, const T* __restrict__ U, const T* __restrict__ V,
     const T* __restrict__ Phi, const T* __restrict__ pi, const double* __restrict__ Ubar,
     const double* __restrict__ Vbar, const T* Ub, const T* Vb, const T* Phib, const T* pib, T* Uo, T* Vo, T* Phio,
-    T* pio, double* Ubar_o, double* Vbar_o, const double* Ubar_b, const double* Vbar_b, const T cdt,
-    const TileCtx<T>* tc = nullptr, const bool active = true) {
+    T* pio, double* Ubar_o, double* Vbar_o, const double* Ubar_b, const double* Vbar_b, const T cdt) {
   const int I = g.I, J = g.J, K = g.K;
   constexpr bool ADV = (TERMS & 1) != 0, ADA = (TERMS & 2) != 0;
   const bool hasS = L1 || j < J - 1;   // V row j exists, scalar row j+1 exists
@@ -207,30 +102,10 @@ __device__ __forceinline__ void fused_column(
   const int vfE = L1 ? i : wrapi(i + (Mv - 1) / 2, I), vfW = L1 ? im : wrapi(i - (Mv + 1) / 2, I);
   const int gE = L1 ? i : wrapi(i + (M1 - 1) / 2, I), gW = L1 ? im : wrapi(i - (M1 + 1) / 2, I);
 
-  // ---- indices of the level loads: shared-memory tile or global rows
-  int lr0 = rj, lrN = rjm, lrS = rjp;
-  int li = i, lie = ie, liw = iw, lfE = fE, lfE1 = fE1, lfW = fW, lfW1 = fW1, lip = ip, lim = im;
-  int lvie = vie, lviw = viw, lvfE = vfE, lvfW = vfW, lgE = gE, lgW = gW;
-  if (TILE) {
-    lr0 = (1 + tc->ty) * kPitch;
-    lrN = tc->ty * kPitch;
-    lrS = (2 + tc->ty) * kPitch;
-    li = tc->tx + tc->H;
-    lie = li + M;
-    liw = li - M;
-    lfE = li + (M - 1) / 2;
-    lfE1 = li + (M + 1) / 2;
-    lfW = li - (M + 1) / 2;
-    lfW1 = li - (M - 1) / 2;
-    lip = li + 1;
-    lim = li - 1;
-    lvie = li + Mv;
-    lviw = li - Mv;
-    lvfE = li + (Mv - 1) / 2;
-    lvfW = li - (Mv + 1) / 2;
-    lgE = li + (M1 - 1) / 2;
-    lgW = li - (M1 + 1) / 2;
-  }
+  // ---- indices of the level loads
+  const int lr0 = rj, lrN = rjm, lrS = rjp;
+  const int li = i, lie = ie, liw = iw, lfE = fE, lfE1 = fE1, lfW = fW, lfW1 = fW1, lip = ip, lim = im;
+  const int lvie = vie, lviw = viw, lvfE = vfE, lvfW = vfW, lgE = gE, lgW = gW;
 
   // ---- column state a2 from pi (level independent)
   auto mass = [&](int r, int c) { return g.pit[r + c] + pi[r + c]; };
@@ -292,13 +167,11 @@ __device__ __forceinline__ void fused_column(
     Cs = ((double)PugE * Ubar[rjp + gE] - (double)PugW * Ubar[rjp + gW]) * (double)rdxs +
          ((hasSS ? (double)svjp * (double)Pvs * Vbar[rjp + i] : 0.0) - (double)svj * (double)Pvc * Vbar[rj + i]) *
              (double)rdys;
-  if (active) {
-    if (MODE == 0)
-      pio[rj + i] = ADA ? (T)(-Cc) : T(0);
-    else {
-      const double pb = (MODE == 1) ? (double)pi[rj + i] : (double)pib[rj + i];
-      pio[rj + i] = ADA ? (T)(pb - (double)cdt * Cc) : (T)pb;
-    }
+  if (MODE == 0)
+    pio[rj + i] = ADA ? (T)(-Cc) : T(0);
+  else {
+    const double pb = (MODE == 1) ? (double)pi[rj + i] : (double)pib[rj + i];
+    pio[rj + i] = ADA ? (T)(pb - (double)cdt * Cc) : (T)pb;
   }
   const T Cf = (T)Cc, Cpf = (T)Cp, Csf = (T)Cs;
 
@@ -314,10 +187,6 @@ __device__ __forceinline__ void fused_column(
   double ubar = 0.0, vbar = 0.0;
   T dubar = T(0), dvbar = T(0);
 
-  if (TILE) {  // prime the ring with the two lowest levels
-    tile_issue(*tc, g, U, Phi, V, K - 1, 0);
-    if (K >= 2) tile_issue(*tc, g, U, Phi, V, K - 2, 1);
-  }
   // software pipeline: the geometry of a level is loaded one iteration before
   // its level is computed, and the base state of a level one iteration before
   // that level is completed and written
@@ -341,23 +210,9 @@ __device__ __forceinline__ void fused_column(
         nbPh = Phib[(size_t)k * plane + o_own];
         if (hasS) nbV = Vb[(size_t)k * vplane + o_own];
       }
-      const T* Uk;
-      const T* Phk;
-      const T* Vk;
-      if (TILE) {
-        // the slot of level k+1 was released at the end of the last iteration
-        if (k >= 2) tile_issue(*tc, g, U, Phi, V, k - 2, (it + 2) % kStages);
-        const int slot = it % kStages;
-        mbar_wait(tc->bar + slot, (unsigned)((it / kStages) & 1), tc->err);
-        const T* sb = tc->buf + (size_t)slot * 3 * kTileRows * kPitch;
-        Uk = sb;
-        Phk = sb + kTileRows * kPitch;
-        Vk = sb + 2 * kTileRows * kPitch;
-      } else {
-        Uk = U + (size_t)k * plane;
-        Phk = Phi + (size_t)k * plane;
-        Vk = V + (size_t)k * vplane;
-      }
+      const T* Uk = U + (size_t)k * plane;
+      const T* Phk = Phi + (size_t)k * plane;
+      const T* Vk = V + (size_t)k * vplane;
       const T dsk = q_ds, Hkk = q_H, hk = q_hk, hkr = q_hr, r2dsk = q_r2, onems = q_om, rho = q_rho;
       c_r2 = q_r2;
       c_ds = q_ds;
@@ -477,10 +332,8 @@ __device__ __forceinline__ void fused_column(
       const size_t o = (size_t)kk * plane + rj + i;
       const T bPh = MODE == 0 ? T(0) : pbPh, bU = MODE == 0 ? T(0) : pbU;
       const T oPh = bPh + cdt * TPh, oU = bU + cdt * TU;
-      if (active) {
-        Phio[o] = oPh;
-        Uo[o] = oU;
-      }
+      Phio[o] = oPh;
+      Uo[o] = oU;
       if (kInc) {
         dubar += p_ds * (oU - bU);
       } else {
@@ -491,7 +344,7 @@ __device__ __forceinline__ void fused_column(
         const size_t ov = (size_t)kk * vplane + rj + i;
         const T bV = MODE == 0 ? T(0) : pbV;
         const T oV = bV + cdt * TV;
-        if (active) Vo[ov] = oV;
+        Vo[ov] = oV;
         if (kInc)
           dvbar += p_ds * (oV - bV);
         else
@@ -513,9 +366,8 @@ __device__ __forceinline__ void fused_column(
     pbU = nbU;
     pbV = nbV;
     pbPh = nbPh;
-    if (TILE && k >= 0) __syncthreads();  // every thread is done with this level's slot
   }
-  if (Ubar_o && active) {
+  if (Ubar_o) {
     if (kInc) {
       ubar = Ubar_b[rj + i] + (double)dubar;
       if (hasS) vbar = Vbar_b[rj + i] + (double)dvbar;
@@ -525,75 +377,24 @@ __device__ __forceinline__ void fused_column(
   }
 }
 
-// BY = 1: one warp per block covering 32 columns of one row, loads from
-// global memory (the row index is warp-uniform, so row tables sit in uniform
-// registers); PART picks the rows of the launch.  BY = kTileY: a 32 x 4 tile
-// whose levels are staged in shared memory by the TMA bulk-copy engine (global
-// loads where the halo is too wide).
-template <class T, int MODE, int BY, int TERMS = 3, bool NL = false, int PART = 0>
-__global__ void __launch_bounds__(kTileX* BY, BY == 1 ? (sizeof(T) == 4 ? (PART == 2 ? AGCM_FUSED_MINB_L1 : AGCM_FUSED_MINB) : AGCM_FUSED_MINB64)
-                                                      : (sizeof(T) == 4 ? AGCM_TILE_MINB : 2))
+// One warp per block covering 32 columns of one row, loads from global
+// memory (the row index is warp-uniform, so row tables sit in uniform
+// registers); PART picks the rows of the launch: 0 every row, 1 the rows
+// outside the stride-1 band [l1lo, l1hi), 2 the band, with the stride-1 body.
+template <class T, int MODE, int TERMS = 3, bool NL = false, int PART = 0>
+__global__ void __launch_bounds__(kTileX, sizeof(T) == 4 ? (PART == 2 ? AGCM_FUSED_MINB_L1 : AGCM_FUSED_MINB)
+                                                          : AGCM_FUSED_MINB64)
     k_fused_stage(Geom<T> g, const T* __restrict__ U, const T* __restrict__ V, const T* __restrict__ Phi,
                   const T* __restrict__ pi, const double* __restrict__ Ubar, const double* __restrict__ Vbar,
                   const T* Ub, const T* Vb, const T* Phib, const T* pib, T* Uo, T* Vo, T* Phio, T* pio,
-                  double* Ubar_o, double* Vbar_o, const double* Ubar_b, const double* Vbar_b, T cdt,
-                  int tile_enable, int* err) {
-  const int tx = threadIdx.x;
-  if (BY == 1) {
-    // PART 0: every row; 1: the rows outside the stride-1 band [l1lo, l1hi);
-    // 2: the band, with the stride-1 column body
-    const int i = blockIdx.x * kTileX + tx;
-    int j = blockIdx.y;
-    if (PART == 1 && j >= g.l1lo) j += g.l1hi - g.l1lo;
-    if (PART == 2) j += g.l1lo;
-    if (i < g.I)
-      fused_column<T, MODE, false, TERMS, NL, PART == 2>(g, i, j, U, V, Phi, pi, Ubar, Vbar, Ub, Vb, Phib, pib, Uo, Vo,
-                                                         Phio, pio, Ubar_o, Vbar_o, Ubar_b, Vbar_b, cdt);
-    return;
-  }
-  const int ty = threadIdx.y;
-  const int i0 = blockIdx.x * kTileX, j0 = blockIdx.y * BY;
-  const int i = i0 + tx, j = j0 + ty;
-  const bool active = i < g.I && j < g.J;
-  // halo: the largest stride of the scalar and V rows this tile touches, + 1, to a multiple of 4
-  int Mmax = 1;
-  for (int r = j0 - 1; r <= j0 + BY; ++r) {
-    if (r >= 0 && r < g.J) Mmax = max(Mmax, g.Mu[r]);
-    if (r >= 0 && r < g.J - 1) Mmax = max(Mmax, g.Mv[r]);
-  }
-  const int H = (Mmax + 4) & ~3;
-  const bool tile = tile_enable && H <= kHaloMax && (g.I % 4) == 0 && kTileX + 2 * H <= g.I;
-  if (!tile) {
-    if (active)
-      fused_column<T, MODE, false, TERMS>(g, i, j, U, V, Phi, pi, Ubar, Vbar, Ub, Vb, Phib, pib, Uo, Vo, Phio, pio, Ubar_o,
-                                   Vbar_o, Ubar_b, Vbar_b, cdt);
-    return;
-  }
-  extern __shared__ __align__(128) unsigned char smem[];
-  TileCtx<T> t;
-  t.bar = reinterpret_cast<uint64_t*>(smem);
-  t.buf = reinterpret_cast<T*>(smem + 64);
-  t.H = H;
-  t.i0 = i0;
-  t.j0 = j0;
-  t.tx = tx;
-  t.ty = ty;
-  t.tid = ty * kTileX + tx;
-  t.err = err;
-  int rows_s = 0, rows_v = 0;
-  for (int r = 0; r < kTileRows; ++r) {
-    const int row = j0 - 1 + r;
-    rows_s += (row >= 0 && row < g.J) ? 1 : 0;
-    rows_v += (row >= 0 && row < g.J - 1) ? 1 : 0;
-  }
-  t.tx_bytes = (unsigned)((2 * rows_s + rows_v) * (kTileX + 2 * H) * sizeof(T));
-  if (t.tid == 0) {
-    for (int q = 0; q < kStages; ++q) mbar_init(t.bar + q, 1);
-    mbar_fence_init();
-  }
-  __syncthreads();
-  fused_column<T, MODE, true, TERMS>(g, min(i, g.I - 1), min(j, g.J - 1), U, V, Phi, pi, Ubar, Vbar, Ub, Vb, Phib, pib,
-                              Uo, Vo, Phio, pio, Ubar_o, Vbar_o, Ubar_b, Vbar_b, cdt, &t, active);
+                  double* Ubar_o, double* Vbar_o, const double* Ubar_b, const double* Vbar_b, T cdt) {
+  const int i = blockIdx.x * kTileX + threadIdx.x;
+  int j = blockIdx.y;
+  if (PART == 1 && j >= g.l1lo) j += g.l1hi - g.l1lo;
+  if (PART == 2) j += g.l1lo;
+  if (i < g.I)
+    fused_column<T, MODE, TERMS, NL, PART == 2>(g, i, j, U, V, Phi, pi, Ubar, Vbar, Ub, Vb, Phib, pib, Uo, Vo, Phio,
+                                                pio, Ubar_o, Vbar_o, Ubar_b, Vbar_b, cdt);
 }
 
 // Vertical means Ubar = sum_k dsigma_k U_k, Vbar likewise (FP64), of a state.

@@ -1,9 +1,9 @@
 """agcm_tendency_static: the allocation-free tendency entry point.
 
-Some callers cannot allocate device memory (inside a CUDA-graph capture, under
-a fixed memory budget, or when an embedding application's allocator owns all
-of the GPU).  This entry point takes only the caller's input and output
-buffers and keeps its scratch in a fixed array inside the library.  The test
+Some callers cannot allocate device memory (an application under a fixed
+device-memory budget, or an embedding application whose allocator owns all of
+the GPU).  This entry point takes only the caller's input and output buffers
+and keeps its scratch in a fixed array inside the library.  The test
 checks it, through the C ABI, against agcm_tendency (which allocates its own
 state) on two calls in a row, within the tolerances of the parity tests.
 This file is collected last on purpose.
@@ -83,3 +83,56 @@ def test_static_tendency_with_thermodynamics(cuda_ok, precision, tol):
         assert np.abs(o - r).max() / max(np.abs(r).max(), 1e-300) <= tol, f
     s.close()
     g.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(agcm.AGCM_FP64, 1e-12), (agcm.AGCM_FP32, 1e-6)])
+def test_static_tendency_more_levels_than_columns(cuda_ok, precision, tol):
+    """A 6 x 4 x 30 grid (24 columns, 30 levels) right after a grid with
+    another level count: every level table is rebuilt, none is left over."""
+    import torch
+
+    agcm.build()
+    for I, J, K, seed in [(16, 8, 5, 7), (6, 4, 30, 8), (6, 4, 30, 9)]:
+        st = inputs.baroclinic_jet(I, J, K, seed=seed, noise=1e-2, terrain_seed=2)
+        ones_u, ones_v = np.ones(J, np.int32), np.ones(J - 1, np.int32)
+        g = agcm.Grid(I, J, K, phis=st["phis"], leap_u=ones_u, leap_v=ones_v)
+        s = agcm.State(g, precision)
+        dev_in = {f: torch.as_tensor(np.ascontiguousarray(st[f]), dtype=s.dtype, device="cuda") for f in FIELDS}
+        s.load(dev_in)
+        ref = s.tendency()
+        got = _static_tendency(g, precision, dev_in)
+        torch.cuda.synchronize()
+        for f in FIELDS:
+            r, o = ref[f].double().cpu().numpy(), got[f].double().cpu().numpy()
+            assert np.abs(o - r).max() / max(np.abs(r).max(), 1e-300) <= tol, (I, J, K, f)
+        s.close()
+        g.close()
+
+
+def test_static_tendency_reuses_and_rebuilds_tables(cuda_ok):
+    """Two calls on one grid reuse the tables the first built; a call on a
+    second grid of the same size with other terrain rebuilds them, and a third
+    call on the first grid rebuilds them again."""
+    import torch
+
+    agcm.build()
+    I, J, K = 48, 24, 8
+    prec = agcm.AGCM_FP64
+    sts = [inputs.baroclinic_jet(I, J, K, seed=11, noise=1e-2, terrain_seed=t) for t in (2, 3)]
+    grids = [agcm.Grid(I, J, K, phis=st["phis"]) for st in sts]
+    refs, dev_ins = [], []
+    for g, st in zip(grids, sts):
+        s = agcm.State(g, prec)
+        d = {f: torch.as_tensor(np.ascontiguousarray(st[f]), dtype=s.dtype, device="cuda") for f in FIELDS}
+        s.load(d)
+        refs.append({f: v.double().cpu().numpy() for f, v in s.tendency().items()})
+        dev_ins.append(d)
+        s.close()
+    for q in (0, 0, 1, 0, 1, 1):
+        got = _static_tendency(grids[q], prec, dev_ins[q])
+        torch.cuda.synchronize()
+        for f in FIELDS:
+            r, o = refs[q][f], got[f].double().cpu().numpy()
+            assert np.abs(o - r).max() / max(np.abs(r).max(), 1e-300) <= 1e-12, (q, f)
+    for g in grids:
+        g.close()

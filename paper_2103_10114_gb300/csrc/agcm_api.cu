@@ -24,6 +24,7 @@
 #include "agcm_common.cuh"
 #include "agcm_phases.cuh"
 #include "agcm_fused.cuh"
+#include "agcm_row.cuh"
 #include "agcm_adjoint.cuh"
 #include "agcm_diag.cuh"
 #include "agcm_ensemble.cuh"
@@ -259,6 +260,27 @@ inline void leap1_band(const agcm_grid* g, int* lo, int* hi) {
   *hi = best_hi;
 }
 
+// Work items of the row-segment stage kernel, j << 8 | segment, for every row
+// whose halo leaves at least half of a CTA to owned columns (the grid's rows
+// must be 16-byte aligned, i.e. nlon % 4 == 0), and the rows left to the
+// column kernel.
+inline void row_lists(const agcm_grid* g, std::vector<int>* rowk, std::vector<int>* rowc) {
+  rowk->clear();
+  rowc->clear();
+  for (int j = 0; j < g->J; ++j) {
+    const bool hv = j < g->J - 1;
+    const int H = agcm::row_halo(g->Mu[j], hv ? g->Mv[j] : 1, hv ? g->Mu[j + 1] : 1);
+    int n = 0, S = 0;
+    agcm::row_segments(g->I, H, agcm::kRowB, &n, &S);
+    if (g->I % 4 == 0 && n > 0 && n < 256) {
+      for (int q = 0; q < n; ++q)
+        if (q * S < g->I) rowk->push_back(j << 8 | q);
+    } else {
+      rowc->push_back(j);
+    }
+  }
+}
+
 template <class T>
 int upload_geom(const agcm_grid* g, void** blob_out, agcm::Geom<T>* geom_out) {
   const int I = g->I, J = g->J, K = g->K;
@@ -342,6 +364,12 @@ int upload_geom(const agcm_grid* g, void** blob_out, agcm::Geom<T>* geom_out) {
          o_Avd = putD(g->Av.empty() ? std::vector<double>{0} : g->Av);
   size_t o_rt0 = putT(rt0pit), o_pit = putT(g->pit);
   size_t o_bu = putI(filtU), o_bv = putI(filtV);
+  std::vector<int> rowk, rowc;
+  row_lists(g, &rowk, &rowc);
+  const int nrowk = (int)rowk.size(), nrowc = (int)rowc.size();
+  rowk.push_back(0);
+  rowc.push_back(0);
+  size_t o_rk = putI(rowk), o_rc = putI(rowc);
 
   void* d = dev_alloc(host.size());
   if (!d) return fail(AGCM_ENOMEM, "device allocation of %zu bytes for the grid tables failed", host.size());
@@ -386,6 +414,11 @@ int upload_geom(const agcm_grid* g, void** blob_out, agcm::Geom<T>* geom_out) {
   G.nl = g->beta2 != 0.0 && g->th.delta != 0.0;
   leap1_band(g, &G.l1lo, &G.l1hi);
   G.rady = (T)(1.0 / (kA * g->dth));
+  G.adl = (T)(kA * g->dlam);
+  G.rowk = (const int*)(base + o_rk);
+  G.rowc = (const int*)(base + o_rc);
+  G.nrowk = nrowk;
+  G.nrowc = nrowc;
   *blob_out = d;
   *geom_out = G;
   return AGCM_OK;
@@ -458,50 +491,90 @@ int ensure_bar(agcm_state* s, cudaStream_t st) {
   return AGCM_OK;
 }
 
-// One fused stage: out = base + cdt * T(x[in]) (MODE 1: base = x[in]; MODE 2:
-// base = x[0]; MODE 0: out = T).  Writes the vertical means of out to bar[outb]
-// (outb < 0: not written).
-// Rows launch: the stride-1 band [l1lo, l1hi) with the specialised column
-// body and the other rows with the general one.  Given aux, evf and evj (a
-// second stream and two events), the band runs on aux, forked from st after
-// everything already queued there and joined back before st continues, so the
-// two launches overlap (each fills the other's tail); without them they run
-// one after the other on st.  *launched (optional) receives the number of
-// kernel launches made.
+// One stage: out = base + cdt * T(x[in]) (MODE 1: base = x[in]; MODE 2:
+// base = x[0]; MODE 0: out = T).  Writes the vertical means of out to
+// bar[outb] (outb < 0: not written).
+//
+// Two designs of the stage kernel.  The row-segment kernel (agcm_row.cuh)
+// takes every row whose leap halo fits a CTA, when the rows are 16-byte
+// aligned; the few rows it leaves (the ones next to the poles on fine grids)
+// run the column kernel (agcm_fused.cuh, PART 3).  Grids or buffers the
+// row-segment kernel cannot take run the column kernel on every row, as the
+// stride-1 band (PART 2, specialised body) and the other rows (PART 1).
+// Given aux, evf and evj (a second stream and two events), the smaller launch
+// runs on aux, forked from st after everything already queued there and
+// joined back before st continues, so the two launches overlap; without them
+// they run one after the other on st.  *launched (optional) receives the
+// number of kernel launches made.
+#ifndef AGCM_ROW_KERNEL
+#define AGCM_ROW_KERNEL 1
+#endif
 template <class T, int MODE, int TERMS = 3>
 int launch_fused(const agcm::Geom<T>& G, const void* const xs[4], const double* ub, const double* vb,
                  const void* const xb[4], void* const out[4], double* ubo, double* vbo, const double* ubb,
                  const double* vbb, double cdt, int* err, cudaStream_t st, cudaStream_t aux = nullptr,
                  cudaEvent_t evf = nullptr, cudaEvent_t evj = nullptr, int* launched = nullptr) {
   if (launched) *launched = 1;
-  auto rows = [&](auto nl) -> int {  // one warp per 32 columns of a row
-    const dim3 block(agcm::kTileX, 1);
+  const bool fork = aux && evf && evj;
+  auto col_launch = [&](auto nl, auto part, int ny, cudaStream_t q) {
     const unsigned gx = (unsigned)((G.I + agcm::kTileX - 1) / agcm::kTileX);
-    const int nb = G.l1hi - G.l1lo;
-    auto go = [&](auto part, int ny, cudaStream_t q) {
-      agcm::k_fused_stage<T, MODE, TERMS, decltype(nl)::value, decltype(part)::value>
-          <<<dim3(gx, (unsigned)ny), block, 0, q>>>(
-              G, (const T*)xs[0], (const T*)xs[1], (const T*)xs[2], (const T*)xs[3], ub, vb, (const T*)xb[0],
-              (const T*)xb[1], (const T*)xb[2], (const T*)xb[3], (T*)out[0], (T*)out[1], (T*)out[2], (T*)out[3],
-              ubo, vbo, ubb, vbb, (T)cdt);
-    };
-    if (nb <= 0) {
-      go(std::integral_constant<int, 0>{}, G.J, st);
-    } else if (nb == G.J) {
-      go(std::integral_constant<int, 2>{}, nb, st);
+    agcm::k_fused_stage<T, MODE, TERMS, decltype(nl)::value, decltype(part)::value>
+        <<<dim3(gx, (unsigned)ny), agcm::kTileX, 0, q>>>(
+            G, (const T*)xs[0], (const T*)xs[1], (const T*)xs[2], (const T*)xs[3], ub, vb, (const T*)xb[0],
+            (const T*)xb[1], (const T*)xb[2], (const T*)xb[3], (T*)out[0], (T*)out[1], (T*)out[2], (T*)out[3],
+            ubo, vbo, ubb, vbb, (T)cdt);
+  };
+  auto two = [&](auto first, auto second) -> int {  // first on aux (forked), second on st
+    if (fork) {
+      CUDA_TRY(cudaEventRecord(evf, st));
+      CUDA_TRY(cudaStreamWaitEvent(aux, evf, 0));
+    }
+    first(fork ? aux : st);
+    second(st);
+    if (fork) {
+      CUDA_TRY(cudaEventRecord(evj, aux));
+      CUDA_TRY(cudaStreamWaitEvent(st, evj, 0));
+    }
+    if (launched) *launched = 2;
+    return AGCM_OK;
+  };
+  auto a16 = [](const void* p) { return ((uintptr_t)p & 15) == 0; };
+  bool rowpath = AGCM_ROW_KERNEL && G.nrowk > 0 && a16(xs[0]) && a16(xs[1]) && a16(xs[2]);
+  if (MODE == 2) rowpath = rowpath && a16(xb[0]) && a16(xb[1]) && a16(xb[2]);
+  const size_t smem = agcm::row_smem_bytes<T>(agcm::kRowB, G.K);
+  if (smem > 227 * 1024) rowpath = false;
+  auto rows = [&](auto nl) -> int {
+    if (rowpath) {
+      auto kern = agcm::k_row_stage<T, MODE, TERMS, decltype(nl)::value>;
+      static std::atomic<size_t> attr{0};  // per instantiation: the size set so far
+      if (attr.load() < smem) {
+        CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr.store(smem);
+      }
+      agcm::RowArgs<T> ra{(const T*)xs[0], (const T*)xs[1], (const T*)xs[2], (const T*)xs[3], ub, vb,
+                          (const T*)xb[0], (const T*)xb[1], (const T*)xb[2], (const T*)xb[3], (T*)out[0],
+                          (T*)out[1], (T*)out[2], (T*)out[3], ubo, vbo, ubb, vbb, (T)cdt, G.rowk, err};
+      auto row_go = [&](cudaStream_t q) {
+        kern<<<(unsigned)G.nrowk, agcm::kRowB, smem, q>>>(G, ra);
+      };
+      if (G.nrowc > 0) {
+        int rc = two([&](cudaStream_t q) { col_launch(nl, std::integral_constant<int, 3>{}, G.nrowc, q); },
+                     row_go);
+        if (rc) return rc;
+      } else {
+        row_go(st);
+      }
     } else {
-      const bool fork = aux && evf && evj;
-      if (fork) {
-        CUDA_TRY(cudaEventRecord(evf, st));
-        CUDA_TRY(cudaStreamWaitEvent(aux, evf, 0));
+      const int nb = G.l1hi - G.l1lo;
+      if (nb <= 0) {
+        col_launch(nl, std::integral_constant<int, 0>{}, G.J, st);
+      } else if (nb == G.J) {
+        col_launch(nl, std::integral_constant<int, 2>{}, nb, st);
+      } else {
+        int rc = two([&](cudaStream_t q) { col_launch(nl, std::integral_constant<int, 2>{}, nb, q); },
+                     [&](cudaStream_t q) { col_launch(nl, std::integral_constant<int, 1>{}, G.J - nb, q); });
+        if (rc) return rc;
       }
-      go(std::integral_constant<int, 2>{}, nb, fork ? aux : st);
-      go(std::integral_constant<int, 1>{}, G.J - nb, st);
-      if (fork) {
-        CUDA_TRY(cudaEventRecord(evj, aux));
-        CUDA_TRY(cudaStreamWaitEvent(st, evj, 0));
-      }
-      if (launched) *launched = 2;
     }
     CUDA_TRY(cudaGetLastError());
     return AGCM_OK;
@@ -1206,7 +1279,10 @@ constexpr size_t kOffRowT = kOffInt + 2 * kRowB;     // 12 typed row arrays
 constexpr size_t kOffLevT = kOffRowT + 12 * kRowB;   // 7 typed level arrays
 constexpr size_t kOffColT = kOffLevT + 7 * kLevB;    // pit, rt0pit (typed)
 constexpr size_t kOffBar = kOffColT + 2 * kColB;     // Ubar, Vbar (double)
-constexpr size_t kStaticBytes = kOffBar + 2 * kColB; // about 13 MB
+constexpr size_t kOffRowL = kOffBar + 2 * kColB;     // row-segment items, then column-kernel rows (int)
+constexpr size_t kItemB = al256((kStaticCols / 128 + kStaticRows) * 4);  // at most ceil(nlon/128) items a row
+constexpr size_t kOffErr = kOffRowL + kItemB + al256(kStaticRows * 4);  // status word of the stage kernel
+constexpr size_t kStaticBytes = kOffErr + 256;       // about 13 MB
 
 }  // namespace
 
@@ -1304,6 +1380,16 @@ int tendency_static(const agcm_grid* g, char* base, bool tables, const void* U, 
   CUDA_TRY(cudaMemcpyAsync(Mu, g->Mu.data(), g->Mu.size() * sizeof(int), cudaMemcpyHostToDevice, st));
   if (!g->Mv.empty())
     CUDA_TRY(cudaMemcpyAsync(Mv, g->Mv.data(), g->Mv.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  {
+    std::vector<int> rk, rc;
+    row_lists(g, &rk, &rc);
+    if (!rk.empty())
+      CUDA_TRY(cudaMemcpyAsync(base + kOffRowL, rk.data(), rk.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    if (!rc.empty())
+      CUDA_TRY(cudaMemcpyAsync(base + kOffRowL + kItemB, rc.data(), rc.size() * sizeof(int),
+                               cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemsetAsync(base + kOffErr, 0, sizeof(int), st));
+  }
   k_static_geom<T><<<nblocks(std::max<size_t>((size_t)I * J, (size_t)K), 256), 256, 0, st>>>(
       I, J, K, raw, rawlev, pitraw, Mu, Mv, rowT, levT, colT, rS, lS, cS, g->beta2);
   CUDA_TRY(cudaGetLastError());
@@ -1328,13 +1414,23 @@ int tendency_static(const agcm_grid* g, char* base, bool tables, const void* U, 
   G.pit = colT;
   G.rt0pit = colT + cS;
   G.rady = (T)(1.0 / (kA * g->dth));
+  G.adl = (T)(kA * g->dlam);
+  {
+    std::vector<int> rk, rc;
+    row_lists(g, &rk, &rc);  // host only: counts (the lists were copied with the tables)
+    G.nrowk = (int)rk.size();
+    G.nrowc = (int)rc.size();
+    G.rowk = (const int*)(base + kOffRowL);
+    G.rowc = (const int*)(base + kOffRowL + kItemB);
+  }
   double* ubar = (double*)(base + kOffBar);
   double* vbar = (double*)(base + kOffBar + kColB);
   agcm::k_vsum<T><<<nblocks((size_t)I * J, 256), 256, 0, st>>>(G, (const T*)U, (const T*)V, ubar, vbar);
   const void* xs[4] = {U, V, Phi, pi};
   const void* none[4] = {nullptr, nullptr, nullptr, nullptr};
   void* out[4] = {tU, tV, tPhi, tpi};
-  return launch_fused<T, 0>(G, xs, ubar, vbar, none, out, nullptr, nullptr, nullptr, nullptr, 1.0, nullptr, st);
+  return launch_fused<T, 0>(G, xs, ubar, vbar, none, out, nullptr, nullptr, nullptr, nullptr, 1.0,
+                            (int*)(base + kOffErr), st);
 }
 
 }  // namespace

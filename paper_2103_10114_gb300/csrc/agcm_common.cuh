@@ -54,6 +54,12 @@ struct Geom {
   int nl;           // 1: the delta kappa Phi/P term is on (beta2 != 0)
   int l1lo, l1hi;   // rows [l1lo, l1hi): interior rows whose strides Mu_j, Mv_j, Mu_{j+1} are all 1
   T rady;           // 1 / (a dth)
+  T adl;            // a dlam
+  // work items of the row-segment stage kernel (agcm_row.cuh), j << 8 | segment,
+  // and the rows left to the column kernel (agcm_fused.cuh)
+  const int* rowk;
+  const int* rowc;
+  int nrowk, nrowc;
 };
 
 __device__ __forceinline__ int wrapi(int i, int I) {

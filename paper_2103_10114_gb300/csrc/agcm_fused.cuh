@@ -380,7 +380,8 @@ __device__ __forceinline__ void fused_column(
 // One warp per block covering 32 columns of one row, loads from global
 // memory (the row index is warp-uniform, so row tables sit in uniform
 // registers); PART picks the rows of the launch: 0 every row, 1 the rows
-// outside the stride-1 band [l1lo, l1hi), 2 the band, with the stride-1 body.
+// outside the stride-1 band [l1lo, l1hi), 2 the band, with the stride-1 body,
+// 3 the rows g.rowc (those the row-segment kernel leaves).
 template <class T, int MODE, int TERMS = 3, bool NL = false, int PART = 0>
 __global__ void __launch_bounds__(kTileX, sizeof(T) == 4 ? (PART == 2 ? AGCM_FUSED_MINB_L1 : AGCM_FUSED_MINB)
                                                           : AGCM_FUSED_MINB64)
@@ -392,6 +393,7 @@ __global__ void __launch_bounds__(kTileX, sizeof(T) == 4 ? (PART == 2 ? AGCM_FUS
   int j = blockIdx.y;
   if (PART == 1 && j >= g.l1lo) j += g.l1hi - g.l1lo;
   if (PART == 2) j += g.l1lo;
+  if (PART == 3) j = g.rowc[j];
   if (i < g.I)
     fused_column<T, MODE, TERMS, NL, PART == 2>(g, i, j, U, V, Phi, pi, Ubar, Vbar, Ub, Vb, Phib, pib, Uo, Vo, Phio,
                                                 pio, Ubar_o, Vbar_o, Ubar_b, Vbar_b, cdt);

@@ -262,22 +262,30 @@ inline void leap1_band(const agcm_grid* g, int* lo, int* hi) {
 
 // Work items of the row-segment stage kernel, j << 8 | segment, for every row
 // whose halo leaves at least half of a CTA to owned columns (the grid's rows
-// must be 16-byte aligned, i.e. nlon % 4 == 0), and the rows left to the
-// column kernel.
-inline void row_lists(const agcm_grid* g, std::vector<int>* rowk, std::vector<int>* rowc) {
-  rowk->clear();
+// must be 16-byte aligned, i.e. nlon % 4 == 0), in three classes: rows whose
+// strides Mu_j, Mv_j, Mu_{j+1} are all 1, all 3, and the others (nk[c] items
+// each, listed in that order); and the rows left to the column kernel.
+inline void row_lists(const agcm_grid* g, std::vector<int>* rowk, std::vector<int>* rowc, int nk[3]) {
+  std::vector<int> cls[3];
   rowc->clear();
   for (int j = 0; j < g->J; ++j) {
     const bool hv = j < g->J - 1;
-    const int H = agcm::row_halo(g->Mu[j], hv ? g->Mv[j] : 1, hv ? g->Mu[j + 1] : 1);
+    const int Mu = g->Mu[j], Mv = hv ? g->Mv[j] : Mu, M1 = hv ? g->Mu[j + 1] : Mu;
+    const int H = agcm::row_halo(Mu, hv ? Mv : 1, hv ? M1 : 1);
     int n = 0, S = 0;
     agcm::row_segments(g->I, H, agcm::kRowB, &n, &S);
     if (g->I % 4 == 0 && n > 0 && n < 256) {
+      const int c = (Mu == Mv && Mu == M1 && (Mu == 1 || Mu == 3)) ? (Mu == 1 ? 0 : 1) : 2;
       for (int q = 0; q < n; ++q)
-        if (q * S < g->I) rowk->push_back(j << 8 | q);
+        if (q * S < g->I) cls[c].push_back(j << 8 | q);
     } else {
       rowc->push_back(j);
     }
+  }
+  rowk->clear();
+  for (int c = 0; c < 3; ++c) {
+    nk[c] = (int)cls[c].size();
+    rowk->insert(rowk->end(), cls[c].begin(), cls[c].end());
   }
 }
 
@@ -365,8 +373,9 @@ int upload_geom(const agcm_grid* g, void** blob_out, agcm::Geom<T>* geom_out) {
   size_t o_rt0 = putT(rt0pit), o_pit = putT(g->pit);
   size_t o_bu = putI(filtU), o_bv = putI(filtV);
   std::vector<int> rowk, rowc;
-  row_lists(g, &rowk, &rowc);
-  const int nrowk = (int)rowk.size(), nrowc = (int)rowc.size();
+  int nk[3];
+  row_lists(g, &rowk, &rowc, nk);
+  const int nrowc = (int)rowc.size();
   rowk.push_back(0);
   rowc.push_back(0);
   size_t o_rk = putI(rowk), o_rc = putI(rowc);
@@ -417,7 +426,7 @@ int upload_geom(const agcm_grid* g, void** blob_out, agcm::Geom<T>* geom_out) {
   G.adl = (T)(kA * g->dlam);
   G.rowk = (const int*)(base + o_rk);
   G.rowc = (const int*)(base + o_rc);
-  G.nrowk = nrowk;
+  for (int c = 0; c < 3; ++c) G.nk[c] = nk[c];
   G.nrowc = nrowc;
   *blob_out = d;
   *geom_out = G;
@@ -539,31 +548,47 @@ int launch_fused(const agcm::Geom<T>& G, const void* const xs[4], const double* 
     return AGCM_OK;
   };
   auto a16 = [](const void* p) { return ((uintptr_t)p & 15) == 0; };
-  bool rowpath = AGCM_ROW_KERNEL && G.nrowk > 0 && a16(xs[0]) && a16(xs[1]) && a16(xs[2]);
+  bool rowpath = AGCM_ROW_KERNEL && G.nk[0] + G.nk[1] + G.nk[2] > 0 && a16(xs[0]) && a16(xs[1]) && a16(xs[2]);
   if (MODE == 2) rowpath = rowpath && a16(xb[0]) && a16(xb[1]) && a16(xb[2]);
   const size_t smem = agcm::row_smem_bytes<T>(agcm::kRowB, G.K);
   if (smem > 227 * 1024) rowpath = false;
   auto rows = [&](auto nl) -> int {
     if (rowpath) {
-      auto kern = agcm::k_row_stage<T, MODE, TERMS, decltype(nl)::value>;
-      static std::atomic<size_t> attr{0};  // per instantiation: the size set so far
-      if (attr.load() < smem) {
-        CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr.store(smem);
-      }
       agcm::RowArgs<T> ra{(const T*)xs[0], (const T*)xs[1], (const T*)xs[2], (const T*)xs[3], ub, vb,
                           (const T*)xb[0], (const T*)xb[1], (const T*)xb[2], (const T*)xb[3], (T*)out[0],
                           (T*)out[1], (T*)out[2], (T*)out[3], ubo, vbo, ubb, vbb, (T)cdt, G.rowk, err};
-      auto row_go = [&](cudaStream_t q) {
-        kern<<<(unsigned)G.nrowk, agcm::kRowB, smem, q>>>(G, ra);
+      int nlaunch = 0;
+      // one launch per stride class: class c takes items [b, b + nk[c])
+      auto cls_go = [&](auto mc, int c, cudaStream_t q) -> int {
+        if (G.nk[c] == 0) return AGCM_OK;
+        auto kern = agcm::k_row_stage<T, MODE, TERMS, decltype(nl)::value, decltype(mc)::value>;
+        static std::atomic<size_t> attr{0};  // per instantiation: the size set so far
+        if (attr.load() < smem) {
+          CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+          attr.store(smem);
+        }
+        agcm::RowArgs<T> rc = ra;
+        rc.rows = G.rowk + (c > 0 ? G.nk[0] : 0) + (c > 1 ? G.nk[1] : 0);
+        kern<<<(unsigned)G.nk[c], agcm::kRowB, smem, q>>>(G, rc);
+        ++nlaunch;
+        return AGCM_OK;
       };
-      if (G.nrowc > 0) {
-        int rc = two([&](cudaStream_t q) { col_launch(nl, std::integral_constant<int, 3>{}, G.nrowc, q); },
-                     row_go);
-        if (rc) return rc;
-      } else {
-        row_go(st);
-      }
+      // the stride-1 rows and the column-kernel rows on the second stream,
+      // the stride-3 and other rows on st
+      int rc = two(
+          [&](cudaStream_t q) {
+            cls_go(std::integral_constant<int, 1>{}, 0, q);
+            if (G.nrowc > 0) {
+              col_launch(nl, std::integral_constant<int, 3>{}, G.nrowc, q);
+              ++nlaunch;
+            }
+          },
+          [&](cudaStream_t q) {
+            cls_go(std::integral_constant<int, 3>{}, 1, q);
+            cls_go(std::integral_constant<int, 0>{}, 2, q);
+          });
+      if (rc) return rc;
+      if (launched) *launched = nlaunch;
     } else {
       const int nb = G.l1hi - G.l1lo;
       if (nb <= 0) {
@@ -1382,7 +1407,8 @@ int tendency_static(const agcm_grid* g, char* base, bool tables, const void* U, 
     CUDA_TRY(cudaMemcpyAsync(Mv, g->Mv.data(), g->Mv.size() * sizeof(int), cudaMemcpyHostToDevice, st));
   {
     std::vector<int> rk, rc;
-    row_lists(g, &rk, &rc);
+    int nk[3];
+    row_lists(g, &rk, &rc, nk);
     if (!rk.empty())
       CUDA_TRY(cudaMemcpyAsync(base + kOffRowL, rk.data(), rk.size() * sizeof(int), cudaMemcpyHostToDevice, st));
     if (!rc.empty())
@@ -1417,8 +1443,7 @@ int tendency_static(const agcm_grid* g, char* base, bool tables, const void* U, 
   G.adl = (T)(kA * g->dlam);
   {
     std::vector<int> rk, rc;
-    row_lists(g, &rk, &rc);  // host only: counts (the lists were copied with the tables)
-    G.nrowk = (int)rk.size();
+    row_lists(g, &rk, &rc, G.nk);  // host only: counts (the lists were copied with the tables)
     G.nrowc = (int)rc.size();
     G.rowk = (const int*)(base + kOffRowL);
     G.rowc = (const int*)(base + kOffRowL + kItemB);

@@ -55,11 +55,13 @@ struct Geom {
   int l1lo, l1hi;   // rows [l1lo, l1hi): interior rows whose strides Mu_j, Mv_j, Mu_{j+1} are all 1
   T rady;           // 1 / (a dth)
   T adl;            // a dlam
-  // work items of the row-segment stage kernel (agcm_row.cuh), j << 8 | segment,
-  // and the rows left to the column kernel (agcm_fused.cuh)
+  // work items of the row-segment stage kernel (agcm_row.cuh), j << 8 | segment:
+  // nk[0] items of rows whose strides are all 1, then nk[1] items of rows
+  // whose strides are all 3, then nk[2] items of the other rows; and the
+  // nrowc rows left to the column kernel (agcm_fused.cuh)
   const int* rowk;
   const int* rowc;
-  int nrowk, nrowc;
+  int nk[3], nrowc;
 };
 
 __device__ __forceinline__ int wrapi(int i, int I) {

@@ -9,22 +9,22 @@
 //   * the raw rows j-1, j, j+1 of U, Phi and V of the stage input (and row j
 //     of the base state x_n in the later stages) arrive in a ring of shared
 //     memory slots by 1-D bulk copies (cp.async.bulk, completing on one
-//     mbarrier per slot), several levels ahead of their use;
-//   * phase A: each thread turns its own column's raw values into the
-//     quantities its neighbours need — the mass fluxes F = P U (Eq. 1's IAP
-//     fluxes), G = F/P of the skew advection, f* U of the Coriolis pair — and
-//     writes them to shared memory;
-//   * phase B: each thread forms the leap divergence D of its column at rows
-//     j and j+1 from the fluxes of its leap partners (Table "Communication
-//     aggregation": the (x+N-1, x-N) pair), advances the column carries of
+//     mbarrier per slot), issued several levels ahead of their use from a
+//     descriptor list built once per CTA;
+//   * own column: each thread forms what its neighbours need — the mass
+//     fluxes F = P U (Eq. 1's IAP fluxes), G = F/P of the skew advection,
+//     f* U of the Coriolis pair — and the leap divergence D of its column at
+//     rows j and j+1 (Table "Communication aggregation": the (x+N-1, x-N)
+//     pair, read from the staged U rows), advances the column carries of
 //     Alg. 1 / Alg. 2 read bottom-up (suffix sums SD of dsigma D, so
 //     W_k = SD_k - (1 - sh_k) C) and of the hydrostatic integral (psi as a
-//     suffix sum of H Phi/P, reading R7), and publishes W and psi;
-//   * phase C: the threads of the owned columns assemble the Phi, U and V
-//     cells (advection L, pressure gradient over the (x+N, x-N+1) pair,
-//     Coriolis pair, Omega~ conversion) from their neighbours' published
-//     values; the vertical advection of a level needs the level above, so each
-//     level is completed and written one iteration later.
+//     suffix sum of H Phi/P, reading R7), and publishes all of it to one of
+//     two shared-memory buffers;
+//   * after one barrier, the owned columns assemble the Phi, U and V cells
+//     (advection L, pressure gradient over the (x+N, x-N+1) pair, Coriolis
+//     pair, Omega~ conversion) from their neighbours' published values; the
+//     vertical advection of a level needs the level above, so each level is
+//     completed and written one iteration later.
 // Nothing is recomputed per neighbour and every stencil read is a 32-bit
 // shared-memory offset fixed for the whole column, which is what the
 // one-thread-per-column global-load kernel (agcm_fused.cuh) spent most of its
@@ -43,10 +43,10 @@ namespace agcm {
 constexpr int kRowB = 256;         // threads per CTA: the widest segment + halo
 constexpr int kRowNP = 13;         // arrays each thread publishes per level
 constexpr int kRowRaw = 12;        // staged rows per level: U, Phi, V at j-1, j, j+1 and x_n's U, Phi, V at j
+constexpr int kRowDesc = 48;       // copy descriptors per CTA: 12 rows of at most 4 pieces
 #ifndef AGCM_ROW_MINB
 #define AGCM_ROW_MINB 3
 #endif
-
 #ifndef AGCM_ROW_R
 #define AGCM_ROW_R 2
 #endif
@@ -86,9 +86,6 @@ __device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
 }
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
 __device__ __forceinline__ bool mbar_try(uint64_t* bar, unsigned parity) {
   unsigned ok;
   asm volatile(
@@ -98,26 +95,28 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, unsigned parity) {
       : "memory");
   return ok != 0;
 }
-// Wait for a slot's copies, at most about a second (2e9 clocks).  On expiry
-// the CTA's abort flag and the status word get AGCM_ETIMEOUT (4); once the
-// flag is set every later wait of the CTA returns at once, so the kernel runs
-// to its end (no thread leaves early, every barrier is still met).
+// Wait for a ring slot's copies: try_wait suspends the thread until the phase
+// completes (or a hardware time limit passes), so the loop turns rarely; it
+// gives up after about a second (2e9 clocks), setting the CTA's abort flag
+// and the status word to AGCM_ETIMEOUT (4).  Once the flag is set every later
+// wait of the CTA returns at once, so the kernel runs to its end (no thread
+// leaves early, every barrier is still met).
 __device__ __forceinline__ void mbar_wait_bounded(uint64_t* bar, unsigned parity, volatile int* abort_flag,
                                                   int* err) {
-  if (mbar_try(bar, parity)) return;
-  const long long t0 = clock64();
+  long long t0 = -1;
   while (!mbar_try(bar, parity)) {
     if (*abort_flag) return;
-    if (clock64() - t0 > 2000000000LL) {
+    const long long now = clock64();
+    if (t0 < 0) t0 = now;
+    if (now - t0 > 2000000000LL) {
       *abort_flag = 1;
       if (err) atomicExch(err, 4);
       return;
     }
   }
 }
-__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_addr(dst)),
+__device__ __forceinline__ void bulk_copy_g2s(unsigned dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                "l"(src), "r"(bytes), "r"(smem_addr(bar))
                : "memory");
 }
@@ -151,61 +150,32 @@ struct RowArgs {
   int* err;          // status word (AGCM_ETIMEOUT)
 };
 
+// One bulk copy of a level: a piece of a staged row, its source at level 0,
+// the plane stride in elements, its destination offset in a ring slot
+// (bytes) and its size in bytes.
+struct RowDesc {
+  const char* src0;
+  unsigned long long plane_bytes;
+  unsigned dst;
+  unsigned bytes;
+};
+
+constexpr size_t kRowHead = 64 + (size_t)kRowDesc * sizeof(RowDesc);
 // Bytes of dynamic shared memory for NTP columns per array and K levels.
 template <class T>
 __host__ __device__ constexpr size_t row_smem_bytes(int NTP, int K) {
-  return 64 + sizeof(T) * (size_t)NTP * (RowCfg<T>::R * kRowRaw + 2 * kRowNP + 2) +
+  return kRowHead + sizeof(T) * (size_t)NTP * (RowCfg<T>::R * kRowRaw + 2 * kRowNP + 2) +
          (size_t)K * (8 * sizeof(T) + sizeof(double));
-}
-
-// The staged row a lane of warp 0 copies every level (lane q: 0..2 U rows
-// j-1, j, j+1; 3..5 Phi; 6..8 V; 9..11 x_n's U, Phi, V at row j): its first
-// element at level 0 (nullptr: the row does not exist or is not staged) and
-// the plane stride.
-template <class T>
-struct RowSrc {
-  const T* row0;
-  size_t plane;
-};
-template <class T>
-__device__ __forceinline__ RowSrc<T> row_src(const RowArgs<T>& a, int q, int I, int J, int j, bool based) {
-  RowSrc<T> s{nullptr, 0};
-  if (q >= kRowRaw || (q >= 9 && !based)) return s;
-  const int f = q < 9 ? q / 3 : q - 9;
-  const int r = q < 9 ? j - 1 + q % 3 : j;
-  const int nrows = f == 2 ? J - 1 : J;
-  if (r < 0 || r >= nrows) return s;
-  const T* fld = q < 9 ? (f == 0 ? a.U : (f == 1 ? a.Phi : a.V)) : (f == 0 ? a.Ub : (f == 1 ? a.Phib : a.Vb));
-  s.row0 = fld + (size_t)r * I;
-  s.plane = (size_t)nrows * I;
-  return s;
-}
-// Issue the bulk copies of staged row q of level k into ring slot `slot`:
-// the segment's NT columns starting at global column cstart = c0 - H
-// (periodic, so a row may come in several pieces).
-template <class T>
-__device__ __forceinline__ void row_issue(const RowSrc<T>& src, T* ring, uint64_t* bar, int I, int k, int slot,
-                                          int NTP, int cstart, int NT, int q) {
-  if (src.row0 == nullptr) return;
-  const T* s = src.row0 + (size_t)k * src.plane;
-  T* dst = ring + ((size_t)slot * kRowRaw + q) * NTP;
-  int pos = cstart, left = NT, off = 0;
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  while (left > 0) {
-    const int len = left < I - pos ? left : I - pos;
-    bulk_copy_g2s(dst + off, s + pos, (unsigned)(len * sizeof(T)), bar + slot);
-    off += len;
-    left -= len;
-    pos = 0;
-  }
 }
 
 // The stage on one row segment.  MODE 0: out = T(x) (validation); MODE 1:
 // base = x (first stage); MODE 2: base = x_n (later stages; may alias out).
 // TERMS: 1 advection, 2 adaptation, 3 both (Eq. 2's split).  NL: Eq. 1's
 // delta kappa Phi/P term (each Phi/P entering psi or the Omega~ coefficient
-// is scaled by 1 + rho_k Phi/P).
-template <class T, int MODE, int TERMS, bool NL>
+// is scaled by 1 + rho_k Phi/P).  MC > 0: every row of the launch has
+// Mu_j = Mv_j = Mu_{j+1} = MC, so the partner offsets are compile-time
+// constants; MC = 0: any strides.
+template <class T, int MODE, int TERMS, bool NL, int MC>
 __global__ void __launch_bounds__(kRowB, sizeof(T) == 4 ? AGCM_ROW_MINB : 2)
     k_row_stage(const Geom<T> g, const RowArgs<T> a) {
   constexpr int R = RowCfg<T>::R;
@@ -215,9 +185,9 @@ __global__ void __launch_bounds__(kRowB, sizeof(T) == 4 ? AGCM_ROW_MINB : 2)
   const int item = a.rows[blockIdx.x];  // row j and segment of this CTA
   const int j = item >> 8, seg = item & 255;
   const bool hasV = j < J - 1;  // V row j (and scalar row j+1) exist
-  const int Mu = g.Mu[j];
-  const int Mv = hasV ? g.Mv[j] : 1;
-  const int M1 = hasV ? g.Mu[j + 1] : 1;
+  const int Mu = MC ? MC : g.Mu[j];
+  const int Mv = MC ? MC : (hasV ? g.Mv[j] : 1);
+  const int M1 = MC ? MC : (hasV ? g.Mu[j + 1] : 1);
   const int H = row_halo(Mu, Mv, M1);
   int nseg, Sw;
   row_segments(I, H, kRowB, &nseg, &Sw);
@@ -228,27 +198,29 @@ __global__ void __launch_bounds__(kRowB, sizeof(T) == 4 ? AGCM_ROW_MINB : 2)
   const int NTW = (NT + 31) & ~31;
   const int t = threadIdx.x;
   if (t >= NTW) return;  // whole warps past the segment
-  const int NTP = kRowB;  // array pitch
+  constexpr int NTP = kRowB;  // array pitch
   const bool owned = t >= H && t < H + Sown;
   const int cstart = ((c0 - H) % I + I) % I;  // global column of thread 0
   int gc = cstart + t;                        // own global column
   while (gc >= I) gc -= I;
 
-  // shared memory: mbarriers (R ring slots, the level barrier) and the abort
-  // flag; the ring of staged raw rows; two buffers of the published arrays;
-  // the P^u rows j and j+1; the level tables
+  // shared memory: ring mbarriers, abort flag, descriptor count; the copy
+  // descriptors; the ring of staged raw rows; two buffers of the published
+  // arrays; the P^u rows j and j+1; the level tables
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
-  uint64_t* lvlbar = bar + R;
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 8 * (R + 1));
-  T* ring = reinterpret_cast<T*>(smem + 64);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 8 * R);
+  int* s_ndesc = reinterpret_cast<int*>(smem + 8 * R + 4);
+  unsigned* s_tx = reinterpret_cast<unsigned*>(smem + 8 * R + 8);
+  RowDesc* desc = reinterpret_cast<RowDesc*>(smem + 64);
+  T* ring = reinterpret_cast<T*>(smem + kRowHead);
   T* dA = ring + (size_t)R * kRowRaw * NTP;            // 2 buffers x kRowNP arrays
   T* puR = dA + (size_t)2 * kRowNP * NTP;              // P^u of row j, then of row j+1
   T* lev = puR + (size_t)2 * NTP;                      // K x 8 level coefficients
   double* levd = reinterpret_cast<double*>(lev + (size_t)8 * K);  // K: dsigma in FP64
   double* q2 = reinterpret_cast<double*>(dA);          // prologue only: P^u Ubar at rows j, j+1
 
-  // ---- set-up: level tables, mbarriers, zero rows the copies never fill
+  // ---- set-up: level tables, mbarriers, copy descriptors, rows the copies never fill
   for (int k = t; k < K; k += NTW) {
     T* L = lev + 8 * k;
     L[0] = g.ds[k];
@@ -261,56 +233,67 @@ __global__ void __launch_bounds__(kRowB, sizeof(T) == 4 ? AGCM_ROW_MINB : 2)
     L[7] = T(0);
     levd[k] = g.dsd[k];
   }
+  const unsigned ring_s = smem_addr(ring);
   if (t == 0) {
     for (int s = 0; s < R; ++s) mbar_init(bar + s, 1);
-    mbar_init(lvlbar, (unsigned)NTW);
     *abort_flag = 0;
-    mbar_fence_init();
-  }
-  {
-    // rows outside the grid stay zero: U/Phi rows j-1 (j = 0) and j+1 (j = J-1),
-    // V rows j-1, j, j+1 outside 0..J-2, x_n's V row j (j = J-1)
+    // one descriptor per piece of every staged row that exists: q = 0..2 U
+    // rows j-1, j, j+1; 3..5 Phi; 6..8 V; 9..11 x_n's U, Phi, V at row j
+    int nd = 0;
+    unsigned tx = 0;
     for (int q = 0; q < kRowRaw; ++q) {
+      if (q >= 9 && MODE != 2) break;
       const int f = q < 9 ? q / 3 : q - 9;
       const int r = q < 9 ? j - 1 + q % 3 : j;
       const int nrows = f == 2 ? J - 1 : J;
-      if (r >= 0 && r < nrows) continue;
-      for (int s = 0; s < R; ++s) ring[((size_t)s * kRowRaw + q) * NTP + t] = T(0);
+      if (r < 0 || r >= nrows) continue;
+      const T* fld = q < 9 ? (f == 0 ? a.U : (f == 1 ? a.Phi : a.V)) : (f == 0 ? a.Ub : (f == 1 ? a.Phib : a.Vb));
+      const T* row = fld + (size_t)r * I;
+      int pos = cstart, left = NT, off = 0;
+      while (left > 0 && nd < kRowDesc) {
+        const int len = left < I - pos ? left : I - pos;
+        desc[nd].src0 = reinterpret_cast<const char*>(row + pos);
+        desc[nd].plane_bytes = (unsigned long long)nrows * I * sizeof(T);
+        desc[nd].dst = (unsigned)(((size_t)q * NTP + off) * sizeof(T));
+        desc[nd].bytes = (unsigned)(len * sizeof(T));
+        tx += desc[nd].bytes;
+        ++nd;
+        off += len;
+        left -= len;
+        pos = 0;
+      }
     }
+    *s_ndesc = nd;
+    *s_tx = tx;
+    mbar_fence_init();
   }
-  unsigned tx_bytes = 0;
   for (int q = 0; q < kRowRaw; ++q) {
+    // rows outside the grid stay zero: U/Phi rows j-1 (j = 0) and j+1 (j = J-1),
+    // V rows j-1, j, j+1 outside 0..J-2, x_n's V row j (j = J-1)
     const int f = q < 9 ? q / 3 : q - 9;
     const int r = q < 9 ? j - 1 + q % 3 : j;
     const int nrows = f == 2 ? J - 1 : J;
-    if (q >= 9 && MODE != 2) break;
-    if (r >= 0 && r < nrows) tx_bytes += (unsigned)(NT * sizeof(T));
+    if (r >= 0 && r < nrows) continue;
+    for (int s = 0; s < R; ++s) ring[((size_t)s * kRowRaw + q) * NTP + t] = T(0);
   }
   row_sync(NTW);
-  // Staged rows are issued by lane 0 of warps: warp w takes rows w, w + nw, ...
-  // (nw = warps of the segment), so no warp carries all the copies of a level;
-  // thread 0 announces each slot's bytes.  Any thread may issue once every
-  // thread has passed the level barrier of the slot's previous level.
+  // Copies of level kk into slot s: thread 0 announces the bytes, and lane 0
+  // of warp w issues descriptors w, w + nw, ... (nw = warps of the segment),
+  // so no warp carries all the copies.
   const int nw = NTW >> 5, lane = t & 31, warp = t >> 5;
-  RowSrc<T> rsrc0{nullptr, 0}, rsrc1{nullptr, 0};  // rows warp and warp + nw (lane 0)
-  if (lane == 0) {
-    rsrc0 = row_src(a, warp, I, J, j, MODE == 2);
-    rsrc1 = row_src(a, warp + nw, I, J, j, MODE == 2);
-  }
-  auto issue_level = [&](int kk, int slot) {
-    if (t == 0) mbar_expect_tx(bar + slot, tx_bytes);
+  const int ndesc = *s_ndesc;
+  const unsigned txb = *s_tx;
+  auto issue_level = [&](int kk, int s) {
+    if (t == 0) mbar_expect_tx(bar + s, txb);
     if (lane == 0) {
-      row_issue(rsrc0, ring, bar, I, kk, slot, NTP, cstart, NT, warp);
-      row_issue(rsrc1, ring, bar, I, kk, slot, NTP, cstart, NT, warp + nw);
-      for (int q = warp + 2 * nw; q < kRowRaw; q += nw)  // segments of fewer than 6 warps
-        row_issue(row_src(a, q, I, J, j, MODE == 2), ring, bar, I, kk, slot, NTP, cstart, NT, q);
+      const unsigned base = ring_s + (unsigned)(s * kRowRaw * NTP * sizeof(T));
+      for (int d = warp; d < ndesc; d += nw) {
+        const RowDesc e = desc[d];
+        bulk_copy_g2s(base + e.dst, e.src0 + (unsigned long long)kk * e.plane_bytes, e.bytes, bar + s);
+      }
     }
   };
-  int last_it = -1;  // iteration index of the last level whose copies were issued (thread 0's record)
-  for (int s = 0; s < R && s < K; ++s) {
-    issue_level(K - 1 - s, s);
-    last_it = s;
-  }
+  for (int s = 0; s < R && s < K; ++s) issue_level(K - 1 - s, s);
 
   // ---- level-independent column quantities of the own column (a2)
   const T one = T(1);
@@ -324,9 +307,9 @@ __global__ void __launch_bounds__(kRowB, sizeof(T) == 4 ? AGCM_ROW_MINB : 2)
     rPc = one / sqrt_t(mc);
     Puc = sqrt_t(T(0.5) * (mc + mcp));
     rPuc = one / Puc;
-    T mn = 0, ms = 0, mss = 0;
+    T ms = 0;
     if (hasN) {
-      mn = mass(j - 1, gc);
+      const T mn = mass(j - 1, gc);
       rPn = one / sqrt_t(mn);
       rPun = one / sqrt_t(T(0.5) * (mn + mass(j - 1, gcp)));
       const T Pvn = sqrt_t(T(0.5) * (mn + mc));
@@ -343,8 +326,7 @@ __global__ void __launch_bounds__(kRowB, sizeof(T) == 4 ? AGCM_ROW_MINB : 2)
       sPvc = g.sv[j] * Pvc;
     }
     if (hasSS) {
-      mss = mass(j + 2, gc);
-      const T Pvs = sqrt_t(T(0.5) * (ms + mss));
+      const T Pvs = sqrt_t(T(0.5) * (ms + mass(j + 2, gc)));
       rPvs = one / Pvs;
       sPvs = g.sv[j + 1] * Pvs;
     }
@@ -364,33 +346,30 @@ __global__ void __launch_bounds__(kRowB, sizeof(T) == 4 ? AGCM_ROW_MINB : 2)
     cotas = g.cota[j + 1];
   }
 
-  // ---- shared-memory offsets of the leap partners, fixed for the column.
-  // A halo thread's partner may lie up to H - 1 columns outside the segment;
-  // such reads land in the neighbouring arrays of the same allocation (the
-  // ring before the published arrays, the P^u rows and level tables after
-  // them) and feed only results that no owned column uses.
-  auto cl = [&](int d) { return t + d; };
-  const int oE = cl((Mu - 1) / 2), oW = cl(-(Mu + 1) / 2);        // F^lambda pair of D (Eq. 6)
-  const int oE1 = cl((Mu + 1) / 2), oW1 = cl(-(Mu - 1) / 2);      // psi pair of the U gradient
-  const int oe = cl(Mu), ow = cl(-Mu);                            // advection partners +-M
-  const int op = cl(1), om = cl(-1);
-  const int ovE = cl((Mv - 1) / 2), ovW = cl(-(Mv + 1) / 2);      // V-cell zonal faces
-  const int ove = cl(Mv), ovw = cl(-Mv);                          // V-cell partners +-Mv
-  const int ogE = cl((M1 - 1) / 2), ogW = cl(-(M1 + 1) / 2);      // D of row j+1
+  // ---- offsets of the leap partners, fixed for the column.  A halo
+  // thread's partner may lie up to H - 1 columns outside the segment; such
+  // reads land in the neighbouring arrays of the same allocation (the ring
+  // before the published arrays, the P^u rows and level tables after them)
+  // and feed only results that no owned column uses.
+  const int dE = (Mu - 1) / 2, dW = -(Mu + 1) / 2;       // F^lambda pair of D (Eq. 6)
+  const int dE1 = (Mu + 1) / 2, dW1 = -(Mu - 1) / 2;     // psi pair of the U gradient
+  const int de = Mu, dw = -Mu;                           // advection partners +-M
+  const int dvE = (Mv - 1) / 2, dvW = -(Mv + 1) / 2;     // V-cell zonal faces
+  const int dve = Mv, dvw = -Mv;                         // V-cell partners +-Mv
+  const int dgE = (M1 - 1) / 2, dgW = -(M1 + 1) / 2;     // D of row j+1
 
   // ---- column integrals C (FP64) of rows j and j+1 from the vertical means
-  {
-    q2[t] = (double)Puc * a.Ubar[(size_t)j * I + gc];
-    q2[NTP + t] = hasS ? (double)Pus * a.Ubar[(size_t)(j + 1) * I + gc] : 0.0;
-    puR[t] = Puc;
-    puR[NTP + t] = Pus;
-  }
+  q2[t] = (double)Puc * a.Ubar[(size_t)j * I + gc];
+  q2[NTP + t] = hasS ? (double)Pus * a.Ubar[(size_t)(j + 1) * I + gc] : 0.0;
+  puR[t] = Puc;
+  puR[NTP + t] = Pus;
   row_sync(NTW);
   const double vbn = hasN ? (double)sPvn * a.Vbar[(size_t)(j - 1) * I + gc] : 0.0;
   const double vbc = hasS ? (double)sPvc * a.Vbar[(size_t)j * I + gc] : 0.0;
   const double vbs = hasSS ? (double)sPvs * a.Vbar[(size_t)(j + 1) * I + gc] : 0.0;
-  const double Cc = (q2[oE] - q2[oW]) * (double)rdx + (vbc - vbn) * (double)rdy;
-  const double Cs = hasS ? (q2[NTP + ogE] - q2[NTP + ogW]) * (double)rdxs + (vbs - vbc) * (double)rdys : 0.0;
+  const double Cc = (q2[t + dE] - q2[t + dW]) * (double)rdx + (vbc - vbn) * (double)rdy;
+  const double Cs =
+      hasS ? (q2[NTP + t + dgE] - q2[NTP + t + dgW]) * (double)rdxs + (vbs - vbc) * (double)rdys : 0.0;
   if (owned) {
     const size_t o = (size_t)j * I + gc;
     if (MODE == 0)
@@ -401,10 +380,8 @@ __global__ void __launch_bounds__(kRowB, sizeof(T) == 4 ? AGCM_ROW_MINB : 2)
     }
   }
   const T Cf = (T)Cc, Csf = (T)Cs;
-  // products of the per-column factors used every level
-  const T kPc = r2A * rPc, kPu = r2A * rPuc, kPv = r2Av * rPvc;
   // the P^u partners of the divergences, fixed for the column
-  const T puE = puR[oE], puW = puR[oW], pusE = puR[NTP + ogE], pusW = puR[NTP + ogW];
+  const T puE = puR[t + dE], puW = puR[t + dW], pusE = puR[NTP + t + dgE], pusW = puR[NTP + t + dgW];
   row_sync(NTW);  // q2 (in the published-array buffers) is free again
 
   // ---- carries down the column
@@ -415,23 +392,23 @@ __global__ void __launch_bounds__(kRowB, sizeof(T) == 4 ? AGCM_ROW_MINB : 2)
   T GsB = 0, GuB = 0, GvB = 0;             // G of the level below
   T PPh = 0, PU = 0, PV = 0;               // partial tendencies of the level below
   T pbU = 0, pbV = 0, pbPh = 0;            // base values of the level below
-  T p_wc = 0, p_wu = 0, p_wv = 0, p_ds = 0;  // level below: r2ds/P (scalar, U, V point; U and V halved), dsigma
+  T p_r2 = 0, p_ds = 0;                    // 1 / (2 dsigma) and dsigma of the level below
   double p_dsd = 0.0;
   double ubar = 0.0, vbar = 0.0;
   T dubar = 0, dvbar = 0;
   const T cdt = a.cdt;
-  const size_t plane = (size_t)J * I, vplane = (size_t)(J - 1) * I;
-  const size_t o_own = (size_t)j * I + gc;
+  // element offsets fit 32 bits: nlon * nlat * nlev <= 4e9
+  const unsigned plane = (unsigned)J * (unsigned)I, vplane = (unsigned)(J - 1) * (unsigned)I;
+  const unsigned o_own = (unsigned)j * (unsigned)I + (unsigned)gc;
 
   // Complete level kk (its partials, base and bottom-face W are the carries)
   // with the top-face vertical flux, which needs G of the level above.
   auto complete = [&](int kk, T Gsc, T Guc, T Gvc) {
-    const T TPh = PPh + (ADV ? (Wb * Gsc) * p_wc : T(0));
-    const T TU = PU + (ADV ? ((Wb + Wbp) * Guc) * p_wu : T(0));
+    const T TPh = PPh + (ADV ? Wb * Gsc * p_r2 * rPc : T(0));
+    const T TU = PU + (ADV ? T(0.5) * (Wb + Wbp) * Guc * p_r2 * rPuc : T(0));
     const T bPh = MODE == 0 ? T(0) : pbPh, bU = MODE == 0 ? T(0) : pbU;
     const T oPh = bPh + cdt * TPh, oU = bU + cdt * TU;
-    // element offsets fit 32 bits: nlon * nlat * nlev <= 4e9
-    const unsigned o = (unsigned)kk * (unsigned)plane + (unsigned)o_own;
+    const unsigned o = (unsigned)kk * plane + o_own;
     if (owned) {
       a.Phio[o] = oPh;
       a.Uo[o] = oU;
@@ -441,10 +418,10 @@ __global__ void __launch_bounds__(kRowB, sizeof(T) == 4 ? AGCM_ROW_MINB : 2)
     else
       ubar += p_dsd * (double)oU;
     if (hasV) {
-      const T TV = PV + (ADV ? ((Wb + Wbs) * Gvc) * p_wv : T(0));
+      const T TV = PV + (ADV ? T(0.5) * (Wb + Wbs) * Gvc * p_r2 * rPvc : T(0));
       const T bV = MODE == 0 ? T(0) : pbV;
       const T oV = bV + cdt * TV;
-      if (owned) a.Vo[(unsigned)kk * (unsigned)vplane + (unsigned)o_own] = oV;
+      if (owned) a.Vo[(unsigned)kk * vplane + o_own] = oV;
       if (kInc)
         dvbar += p_ds * (oV - bV);
       else
@@ -452,28 +429,14 @@ __global__ void __launch_bounds__(kRowB, sizeof(T) == 4 ? AGCM_ROW_MINB : 2)
     }
   };
 
-  // One level; P = the published-array buffer (compile-time, the loop is
-  // unrolled by two), it = iteration count (ring slot and barrier parities).
-  auto level = [&](auto Pc, int k, int it) {
-    constexpr int P = decltype(Pc)::value;
-    T* A = dA + (size_t)P * kRowNP * NTP;
-    T* aGS = A;                // G = Phi/P, row j
-    T* aGU = A + 1 * NTP;      // G = U/P^u, row j
-    T* aGV = A + 2 * NTP;      // G = V/P^v, V row j
-    T* aFL = A + 3 * NTP;      // F^lambda = P^u U, row j
-    T* aFLs = A + 4 * NTP;     // F^lambda, row j+1
-    T* aFTn = A + 5 * NTP;     // sin(theta^v) P^v V, V row j-1
-    T* aFTc = A + 6 * NTP;     // sin(theta^v) P^v V, V row j
-    T* aVn = A + 7 * NTP;      // V, V row j-1
-    T* aVc = A + 8 * NTP;      // V, V row j
-    T* afU = A + 9 * NTP;      // f* U, row j
-    T* afUs = A + 10 * NTP;    // f* U, row j+1
-    T* bPsi = A + 11 * NTP;    // psi, row j
-    T* bW = A + 12 * NTP;      // W at the top face, row j
-    const int slot = R == 2 ? P : it % R;  // iterations alternate the buffers, so with two slots the slot is P
-    mbar_wait_bounded(bar + slot, (unsigned)((it / R) & 1), abort_flag, a.err);
+  int slot = 0;
+  unsigned ph = 0;   // ring slot of the level and the parity of its current use
+  int buf = 0;       // published buffer of the level
+  for (int k = K - 1; k >= 0; --k) {
+    mbar_wait_bounded(bar + slot, ph, abort_flag, a.err);
     const T* rw = ring + (size_t)slot * kRowRaw * NTP;
     const T* raw = rw + t;
+    T* A = dA + (size_t)buf * kRowNP * NTP + t;
     T dsk, Hkk, hk, hkr, r2dsk, onems, rho;
     if constexpr (sizeof(T) == 4) {
       const float4 l0 = reinterpret_cast<const float4*>(lev)[2 * k];
@@ -506,9 +469,9 @@ __global__ void __launch_bounds__(kRowB, sizeof(T) == 4 ? AGCM_ROW_MINB : 2)
     const T Gvc = Vc * rPvc, Gvn = Vn * rPvn, Gvs = Vs * rPvs;
     const T FTn = sPvn * Vn, FTc = sPvc * Vc, FTs = sPvs * Vs;
     // leap divergence (a3) of rows j and j+1 from the staged U rows
-    const T FLe = puE * rw[1 * NTP + oE], FLw = puW * rw[1 * NTP + oW];
+    const T FLe = puE * raw[1 * NTP + dE], FLw = puW * raw[1 * NTP + dW];
     const T D = (FLe - FLw) * rdx + (FTc - FTn) * rdy;
-    const T Ds = (pusE * rw[2 * NTP + ogE] - pusW * rw[2 * NTP + ogW]) * rdxs + (FTs - FTc) * rdys;
+    const T Ds = (pusE * raw[2 * NTP + dgE] - pusW * raw[2 * NTP + dgW]) * rdxs + (FTs - FTc) * rdys;
     // a4: suffix sums -> W at the top face; a5: psi
     SD += dsk * D;
     SDs += dsk * Ds;
@@ -521,67 +484,51 @@ __global__ void __launch_bounds__(kRowB, sizeof(T) == 4 ? AGCM_ROW_MINB : 2)
     const T psi = Hkk * Bc + S, psis = Hkk * Bs + Ss;
     S += hk * Bc;
     Ss += hk * Bs;
-    {  // threads past the segment write slots nobody reads
-      aGS[t] = Gsc;
-      aGU[t] = Guc;
-      aGV[t] = Gvc;
-      aFL[t] = Puc * Uc;
-      aFLs[t] = Pus * Us;
-      aFTn[t] = FTn;
-      aFTc[t] = FTc;
-      aVn[t] = Vn;
-      aVc[t] = Vc;
-      afU[t] = (f0 + Guc * cota) * Uc;
-      afUs[t] = (f0s + Gus * cotas) * Us;
-      bPsi[t] = psi;
-      bW[t] = Wt;
-    }
-    const bool abort_seen = *abort_flag != 0;
-    mbar_arrive(lvlbar);
-    // ---- own-column parts of the cells while the other threads publish
-    const T wc = r2dsk * rPc, wu = T(0.5) * r2dsk * rPuc, wv = T(0.5) * r2dsk * rPvc;
+    // publish (threads past the segment write slots nobody reads)
+    A[0 * NTP] = Gsc;                     // G = Phi/P, row j
+    A[1 * NTP] = Guc;                     // G = U/P^u, row j
+    A[2 * NTP] = Gvc;                     // G = V/P^v, V row j
+    A[3 * NTP] = Puc * Uc;                // F^lambda, row j
+    A[4 * NTP] = Pus * Us;                // F^lambda, row j+1
+    A[5 * NTP] = FTn;                     // sin(theta^v) P^v V, V row j-1
+    A[6 * NTP] = FTc;                     // sin(theta^v) P^v V, V row j
+    A[7 * NTP] = Vn;                      // V, V row j-1
+    A[8 * NTP] = Vc;                      // V, V row j
+    A[9 * NTP] = (f0 + Guc * cota) * Uc;  // f* U, row j
+    A[10 * NTP] = (f0s + Gus * cotas) * Us;  // f* U, row j+1
+    A[11 * NTP] = psi;                    // psi, row j
+    A[12 * NTP] = Wt;                     // W at the top face, row j
+    row_sync(NTW);
+    // every thread is past its reads of this ring slot: fetch level k - R into it
+    if (k - R >= 0) issue_level(k - R, slot);
+    // ---- the cells, from the leap partners' published values
     T nPPh, nPU, nPV = 0;
-    {
+    {  // Phi cell: advection + Omega~ (a7, with Q_k = C - SD_k)
+      const T hor = zf * (FLe * A[0 * NTP + de] - FLw * A[0 * NTP + dw]) + adl * (FTc * Gss - FTn * Gsn);
       const T X = -(NL ? rPc * (one + rho * Gsc) : rPc) * (Hkk * D + hkr * (Cf - SD));
-      const T mer = adl * (FTc * Gss - FTn * Gsn);
-      nPPh = (ADA ? X : T(0)) - (ADV ? mer * kPc + (Wb * GsB) * wc : T(0));
+      nPPh = (ADA ? X : T(0)) - (ADV ? (hor * r2A + Wb * GsB * r2dsk) * rPc : T(0));
     }
-    const T WuBv = ((Wb + Wbp) * GuB) * wu;
-    const T fs = T(0.25) * (f0 + Guc * cota);
-    T vPV = 0;
-    if (hasV) {
-      const T mer = adl2 * ((FTc + FTs) * Gvs - (FTn + FTc) * Gvn);
-      const T pgf = Pvc * (psis - psi) * rady;
-      vPV = (ADV ? -(mer * kPv + ((Wb + Wbs) * GvB) * wv) : T(0)) - (ADA ? pgf : T(0));
-    }
-    if (k + 1 <= K - 1) complete(k + 1, Gsc, Guc, Gvc);
-    mbar_wait_bounded(lvlbar, (unsigned)(it & 1), abort_flag, a.err);
-    // the ring slot of level k is free: fetch level k - R into it.  After a
-    // timeout (abort flag set) nothing more is issued; the flag is read once,
-    // before this level's barrier completed, so every thread decides alike.
-    if (k - R >= 0 && !abort_seen) {
-      issue_level(k - R, slot);
-      last_it = it + R;
-    }
-    // ---- the parts that need the leap partners' published values
-    {  // Phi cell zonal advection
-      const T hor = zf * (FLe * aGS[oe] - FLw * aGS[ow]);
-      if (ADV) nPPh -= hor * kPc;
-    }
-    const T Wtp = bW[op];
+    const T Wtp = A[12 * NTP + 1];
     {  // U cell
-      const T ZE = zf2 * (FLe + aFL[oE1]), ZW = zf2 * (FLw + aFL[oW1]);
-      const T hor = ZE * aGU[oe] - ZW * aGU[ow] + adl2 * ((FTc + aFTc[op]) * Gus - (FTn + aFTn[op]) * Gun);
-      const T pgf = Puc * (bPsi[oE1] - bPsi[oW1]) * rdx;
-      const T vs = Vn + aVn[op] + Vc + aVc[op];
-      nPU = (ADV ? -(hor * kPu + WuBv) : T(0)) - (ADA ? pgf + fs * vs : T(0));
+      const T ZE = zf2 * (FLe + A[3 * NTP + dE1]), ZW = zf2 * (FLw + A[3 * NTP + dW1]);
+      const T hor = ZE * A[1 * NTP + de] - ZW * A[1 * NTP + dw] +
+                    adl2 * ((FTc + A[6 * NTP + 1]) * Gus - (FTn + A[5 * NTP + 1]) * Gun);
+      const T WuB = T(0.5) * (Wb + Wbp);
+      const T pgf = Puc * (A[11 * NTP + dE1] - A[11 * NTP + dW1]) * rdx;
+      const T fs = f0 + Guc * cota;
+      const T vs = Vn + A[7 * NTP + 1] + Vc + A[8 * NTP + 1];
+      nPU = (ADV ? -(hor * r2A + WuB * GuB * r2dsk) * rPuc : T(0)) - (ADA ? pgf + T(0.25) * fs * vs : T(0));
     }
     if (hasV) {  // V cell
-      const T ZE = zfv2 * (aFL[ovE] + aFLs[ovE]), ZW = zfv2 * (aFL[ovW] + aFLs[ovW]);
-      const T hor = ZE * aGV[ove] - ZW * aGV[ovw];
-      const T cor = cn * (afU[om] + afU[t]) + cs * (afUs[om] + afUs[t]);
-      nPV = vPV - (ADV ? hor * kPv : T(0)) + (ADA ? cor : T(0));
+      const T ZE = zfv2 * (A[3 * NTP + dvE] + A[4 * NTP + dvE]), ZW = zfv2 * (A[3 * NTP + dvW] + A[4 * NTP + dvW]);
+      const T hor = ZE * A[2 * NTP + dve] - ZW * A[2 * NTP + dvw] +
+                    adl2 * ((FTc + FTs) * Gvs - (FTn + FTc) * Gvn);
+      const T WvB = T(0.5) * (Wb + Wbs);
+      const T pgf = Pvc * (psis - psi) * rady;
+      const T cor = cn * (A[9 * NTP - 1] + A[9 * NTP]) + cs * (A[10 * NTP - 1] + A[10 * NTP]);
+      nPV = (ADV ? -(hor * r2Av + WvB * GvB * r2dsk) * rPvc : T(0)) + (ADA ? cor - pgf : T(0));
     }
+    if (k + 1 <= K - 1) complete(k + 1, Gsc, Guc, Gvc);
     PPh = nPPh;
     PU = nPU;
     PV = nPV;
@@ -591,22 +538,18 @@ __global__ void __launch_bounds__(kRowB, sizeof(T) == 4 ? AGCM_ROW_MINB : 2)
     GvB = Gvc;
     Wb = Wt;
     Wbs = Wts;
-    p_wc = wc;
-    p_wu = wu;
-    p_wv = wv;
+    p_r2 = r2dsk;
     p_ds = dsk;
     p_dsd = dsd;
     pbU = nbU;
     pbV = nbV;
     pbPh = nbPh;
-  };
-
-  int it = 0, k = K - 1;
-  for (; k >= 1; k -= 2, it += 2) {
-    level(std::integral_constant<int, 0>{}, k, it);
-    level(std::integral_constant<int, 1>{}, k - 1, it + 1);
+    if (++slot == R) {
+      slot = 0;
+      ph ^= 1u;
+    }
+    buf ^= 1;
   }
-  if (k == 0) level(std::integral_constant<int, 0>{}, 0, it);
   // level 0 has no level above: its top-face flux W_0 G_{-1} is zero
   complete(0, T(0), T(0), T(0));
   if (owned && a.Ubar_o) {
@@ -617,20 +560,17 @@ __global__ void __launch_bounds__(kRowB, sizeof(T) == 4 ? AGCM_ROW_MINB : 2)
     a.Ubar_o[o_own] = ubar;
     if (hasV) a.Vbar_o[o_own] = vbar;
   }
-  // after a timeout, wait (bounded) for copies still in flight before the
-  // CTA's shared memory is released
+  // after a timeout, wait (bounded) for the copies still in flight before the
+  // CTA's shared memory is released: the last R levels' phases, then one more
+  // millisecond (copies take microseconds)
   if (t == 0 && *abort_flag) {
-    // the copies of iteration q completed when phase (q / R) & 1 of slot q % R
-    // did; phases of a slot complete in order, so the last R issues suffice
-    for (int q = last_it; q >= 0 && q > last_it - R; --q) {
+    // the level of iteration q sits in slot q % R, use q / R; every level is
+    // issued, the last at iteration K - 1
+    for (int q = K - 1; q >= 0 && q > K - 1 - R; --q) {
       const long long t0 = clock64();
       while (!mbar_try(bar + q % R, (unsigned)((q / R) & 1)) && clock64() - t0 < 2000000000LL) {
       }
     }
-    // threads that saw the flag at different times may have issued copies of
-    // one more level than thread 0 recorded: give any copy still in flight a
-    // further millisecond (copies take microseconds) before the CTA's shared
-    // memory is released
     const long long t1 = clock64();
     while (clock64() - t1 < 2000000LL) {
     }

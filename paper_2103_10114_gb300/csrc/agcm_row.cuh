@@ -115,10 +115,22 @@ __device__ __forceinline__ void mbar_wait_bounded(uint64_t* bar, unsigned parity
     }
   }
 }
-__device__ __forceinline__ void bulk_copy_g2s(unsigned dst, const void* src, unsigned bytes, uint64_t* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-               "l"(src), "r"(bytes), "r"(smem_addr(bar))
-               : "memory");
+// Executed by a whole warp with warp-uniform operands: one elected lane
+// issues the copy (or, with tx != 0, announces tx bytes on the barrier), so
+// the warp does not diverge around it.
+__device__ __forceinline__ void bulk_copy_g2s_warp(unsigned dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "{\n .reg .pred p;\n elect.sync _|p, 0xffffffff;\n"
+      " @p cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n}" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx_warp(uint64_t* bar, unsigned bytes) {
+  asm volatile(
+      "{\n .reg .pred p;\n elect.sync _|p, 0xffffffff;\n"
+      " @p mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n}" ::"r"(smem_addr(bar)),
+      "r"(bytes)
+      : "memory");
 }
 // Named barrier over the CTA's first n threads (n a multiple of 32): warps
 // past the segment leave at the start and take no part.
@@ -277,20 +289,20 @@ __global__ void __launch_bounds__(kRowB, sizeof(T) == 4 ? AGCM_ROW_MINB : 2)
     for (int s = 0; s < R; ++s) ring[((size_t)s * kRowRaw + q) * NTP + t] = T(0);
   }
   row_sync(NTW);
-  // Copies of level kk into slot s: thread 0 announces the bytes, and lane 0
-  // of warp w issues descriptors w, w + nw, ... (nw = warps of the segment),
-  // so no warp carries all the copies.
-  const int nw = NTW >> 5, lane = t & 31, warp = t >> 5;
+  // Copies of level kk into slot s: warp 0 announces the bytes, and warp w
+  // issues descriptors w, w + nw, ... (nw = warps of the segment), so no warp
+  // carries all the copies; the warp index is made warp-uniform so that the
+  // loop and the copies run without divergence.
+  const int nw = NTW >> 5;
+  const int warp = __shfl_sync(0xffffffffu, t >> 5, 0);
   const int ndesc = *s_ndesc;
   const unsigned txb = *s_tx;
   auto issue_level = [&](int kk, int s) {
-    if (t == 0) mbar_expect_tx(bar + s, txb);
-    if (lane == 0) {
-      const unsigned base = ring_s + (unsigned)(s * kRowRaw * NTP * sizeof(T));
-      for (int d = warp; d < ndesc; d += nw) {
-        const RowDesc e = desc[d];
-        bulk_copy_g2s(base + e.dst, e.src0 + (unsigned long long)kk * e.plane_bytes, e.bytes, bar + s);
-      }
+    if (warp == 0) mbar_expect_tx_warp(bar + s, txb);
+    const unsigned base = ring_s + (unsigned)(s * kRowRaw * NTP * sizeof(T));
+    for (int d = warp; d < ndesc; d += nw) {
+      const RowDesc e = desc[d];
+      bulk_copy_g2s_warp(base + e.dst, e.src0 + (unsigned long long)kk * e.plane_bytes, e.bytes, bar + s);
     }
   };
   for (int s = 0; s < R && s < K; ++s) issue_level(K - 1 - s, s);
@@ -498,6 +510,8 @@ __global__ void __launch_bounds__(kRowB, sizeof(T) == 4 ? AGCM_ROW_MINB : 2)
     A[10 * NTP] = (f0s + Gus * cotas) * Us;  // f* U, row j+1
     A[11 * NTP] = psi;                    // psi, row j
     A[12 * NTP] = Wt;                     // W at the top face, row j
+    // the level below is complete now that G of this level is known
+    if (k + 1 <= K - 1) complete(k + 1, Gsc, Guc, Gvc);
     row_sync(NTW);
     // every thread is past its reads of this ring slot: fetch level k - R into it
     if (k - R >= 0) issue_level(k - R, slot);
@@ -528,7 +542,6 @@ __global__ void __launch_bounds__(kRowB, sizeof(T) == 4 ? AGCM_ROW_MINB : 2)
       const T cor = cn * (A[9 * NTP - 1] + A[9 * NTP]) + cs * (A[10 * NTP - 1] + A[10 * NTP]);
       nPV = (ADV ? -(hor * r2Av + WvB * GvB * r2dsk) * rPvc : T(0)) + (ADA ? cor - pgf : T(0));
     }
-    if (k + 1 <= K - 1) complete(k + 1, Gsc, Guc, Gvc);
     PPh = nPPh;
     PU = nPU;
     PV = nPV;

@@ -275,7 +275,8 @@ inline void row_lists(const agcm_grid* g, std::vector<int>* rowk, std::vector<in
     int n = 0, S = 0;
     agcm::row_segments(g->I, H, agcm::kRowB, &n, &S);
     if (g->I % 4 == 0 && n > 0 && n < 256) {
-      const int c = (Mu == Mv && Mu == M1 && (Mu == 1 || Mu == 3)) ? (Mu == 1 ? 0 : 1) : 2;
+      // the last row has no V row: always the general class
+      const int c = (hv && Mu == Mv && Mu == M1 && (Mu == 1 || Mu == 3)) ? (Mu == 1 ? 0 : 1) : 2;
       for (int q = 0; q < n; ++q)
         if (q * S < g->I) cls[c].push_back(j << 8 | q);
     } else {

@@ -40,12 +40,15 @@
 
 namespace agcm {
 
-constexpr int kRowB = 256;         // threads per CTA: the widest segment + halo
+#ifndef AGCM_ROW_B
+#define AGCM_ROW_B 256
+#endif
+constexpr int kRowB = AGCM_ROW_B;  // threads per CTA: the widest segment + halo
 constexpr int kRowNP = 13;         // arrays each thread publishes per level
 constexpr int kRowRaw = 12;        // staged rows per level: U, Phi, V at j-1, j, j+1 and x_n's U, Phi, V at j
 constexpr int kRowDesc = 48;       // copy descriptors per CTA: 12 rows of at most 4 pieces
 #ifndef AGCM_ROW_MINB
-#define AGCM_ROW_MINB 3
+#define AGCM_ROW_MINB (768 / AGCM_ROW_B)  // resident CTAs per SM: 24 warps at <= 80 registers
 #endif
 #ifndef AGCM_ROW_R
 #define AGCM_ROW_R 2
@@ -196,7 +199,7 @@ __global__ void __launch_bounds__(kRowB, sizeof(T) == 4 ? AGCM_ROW_MINB : 2)
   const int I = g.I, J = g.J, K = g.K;
   const int item = a.rows[blockIdx.x];  // row j and segment of this CTA
   const int j = item >> 8, seg = item & 255;
-  const bool hasV = j < J - 1;  // V row j (and scalar row j+1) exist
+  const bool hasV = MC > 0 || j < J - 1;  // V row j (and scalar row j+1) exist; the classes hold no last row
   const int Mu = MC ? MC : g.Mu[j];
   const int Mv = MC ? MC : (hasV ? g.Mv[j] : 1);
   const int M1 = MC ? MC : (hasV ? g.Mu[j + 1] : 1);
@@ -392,6 +395,10 @@ __global__ void __launch_bounds__(kRowB, sizeof(T) == 4 ? AGCM_ROW_MINB : 2)
     }
   }
   const T Cf = (T)Cc, Csf = (T)Cs;
+  // loop-invariant products of the per-column factors
+  const T kPc = r2A * rPc, kPu = r2A * rPuc, kPv = r2Av * rPvc;  // horizontal flux sums -> tendencies
+  const T gU = Puc * rdx, gV = Pvc * rady;                         // pressure-gradient factors
+  const T cota4 = T(0.25) * cota, f04 = T(0.25) * f0;             // a quarter of f* at the U point
   // the P^u partners of the divergences, fixed for the column
   const T puE = puR[t + dE], puW = puR[t + dW], pusE = puR[NTP + t + dgE], pusW = puR[NTP + t + dgW];
   row_sync(NTW);  // q2 (in the published-array buffers) is free again
@@ -404,7 +411,7 @@ __global__ void __launch_bounds__(kRowB, sizeof(T) == 4 ? AGCM_ROW_MINB : 2)
   T GsB = 0, GuB = 0, GvB = 0;             // G of the level below
   T PPh = 0, PU = 0, PV = 0;               // partial tendencies of the level below
   T pbU = 0, pbV = 0, pbPh = 0;            // base values of the level below
-  T p_r2 = 0, p_ds = 0;                    // 1 / (2 dsigma) and dsigma of the level below
+  T p_wc = 0, p_wu = 0, p_wv = 0, p_ds = 0;  // level below: r2ds / P at the scalar point, halved at the U and V points; dsigma
   double p_dsd = 0.0;
   double ubar = 0.0, vbar = 0.0;
   T dubar = 0, dvbar = 0;
@@ -416,8 +423,8 @@ __global__ void __launch_bounds__(kRowB, sizeof(T) == 4 ? AGCM_ROW_MINB : 2)
   // Complete level kk (its partials, base and bottom-face W are the carries)
   // with the top-face vertical flux, which needs G of the level above.
   auto complete = [&](int kk, T Gsc, T Guc, T Gvc) {
-    const T TPh = PPh + (ADV ? Wb * Gsc * p_r2 * rPc : T(0));
-    const T TU = PU + (ADV ? T(0.5) * (Wb + Wbp) * Guc * p_r2 * rPuc : T(0));
+    const T TPh = PPh + (ADV ? (Wb * Gsc) * p_wc : T(0));
+    const T TU = PU + (ADV ? ((Wb + Wbp) * Guc) * p_wu : T(0));
     const T bPh = MODE == 0 ? T(0) : pbPh, bU = MODE == 0 ? T(0) : pbU;
     const T oPh = bPh + cdt * TPh, oU = bU + cdt * TU;
     const unsigned o = (unsigned)kk * plane + o_own;
@@ -430,7 +437,7 @@ __global__ void __launch_bounds__(kRowB, sizeof(T) == 4 ? AGCM_ROW_MINB : 2)
     else
       ubar += p_dsd * (double)oU;
     if (hasV) {
-      const T TV = PV + (ADV ? T(0.5) * (Wb + Wbs) * Gvc * p_r2 * rPvc : T(0));
+      const T TV = PV + (ADV ? ((Wb + Wbs) * Gvc) * p_wv : T(0));
       const T bV = MODE == 0 ? T(0) : pbV;
       const T oV = bV + cdt * TV;
       if (owned) a.Vo[(unsigned)kk * vplane + o_own] = oV;
@@ -482,8 +489,11 @@ __global__ void __launch_bounds__(kRowB, sizeof(T) == 4 ? AGCM_ROW_MINB : 2)
     const T FTn = sPvn * Vn, FTc = sPvc * Vc, FTs = sPvs * Vs;
     // leap divergence (a3) of rows j and j+1 from the staged U rows
     const T FLe = puE * raw[1 * NTP + dE], FLw = puW * raw[1 * NTP + dW];
+    const T FLc = Puc * Uc, FLs = Pus * Us;
+    const T fUc = (f0 + Guc * cota) * Uc, fUs = (f0s + Gus * cotas) * Us;
+    const T FLse = pusE * raw[2 * NTP + dgE], FLsw = pusW * raw[2 * NTP + dgW];
     const T D = (FLe - FLw) * rdx + (FTc - FTn) * rdy;
-    const T Ds = (pusE * raw[2 * NTP + dgE] - pusW * raw[2 * NTP + dgW]) * rdxs + (FTs - FTc) * rdys;
+    const T Ds = (FLse - FLsw) * rdxs + (FTs - FTc) * rdys;
     // a4: suffix sums -> W at the top face; a5: psi
     SD += dsk * D;
     SDs += dsk * Ds;
@@ -500,18 +510,19 @@ __global__ void __launch_bounds__(kRowB, sizeof(T) == 4 ? AGCM_ROW_MINB : 2)
     A[0 * NTP] = Gsc;                     // G = Phi/P, row j
     A[1 * NTP] = Guc;                     // G = U/P^u, row j
     A[2 * NTP] = Gvc;                     // G = V/P^v, V row j
-    A[3 * NTP] = Puc * Uc;                // F^lambda, row j
-    A[4 * NTP] = Pus * Us;                // F^lambda, row j+1
+    A[3 * NTP] = FLc;                     // F^lambda, row j
+    A[4 * NTP] = FLs;                     // F^lambda, row j+1
     A[5 * NTP] = FTn;                     // sin(theta^v) P^v V, V row j-1
     A[6 * NTP] = FTc;                     // sin(theta^v) P^v V, V row j
     A[7 * NTP] = Vn;                      // V, V row j-1
     A[8 * NTP] = Vc;                      // V, V row j
-    A[9 * NTP] = (f0 + Guc * cota) * Uc;  // f* U, row j
-    A[10 * NTP] = (f0s + Gus * cotas) * Us;  // f* U, row j+1
+    A[9 * NTP] = fUc;                     // f* U, row j
+    A[10 * NTP] = fUs;                    // f* U, row j+1
     A[11 * NTP] = psi;                    // psi, row j
     A[12 * NTP] = Wt;                     // W at the top face, row j
     // the level below is complete now that G of this level is known
     if (k + 1 <= K - 1) complete(k + 1, Gsc, Guc, Gvc);
+    const T wc = r2dsk * rPc, wu = T(0.5) * r2dsk * rPuc, wv = T(0.5) * r2dsk * rPvc;
     row_sync(NTW);
     // every thread is past its reads of this ring slot: fetch level k - R into it
     if (k - R >= 0) issue_level(k - R, slot);
@@ -520,27 +531,29 @@ __global__ void __launch_bounds__(kRowB, sizeof(T) == 4 ? AGCM_ROW_MINB : 2)
     {  // Phi cell: advection + Omega~ (a7, with Q_k = C - SD_k)
       const T hor = zf * (FLe * A[0 * NTP + de] - FLw * A[0 * NTP + dw]) + adl * (FTc * Gss - FTn * Gsn);
       const T X = -(NL ? rPc * (one + rho * Gsc) : rPc) * (Hkk * D + hkr * (Cf - SD));
-      nPPh = (ADA ? X : T(0)) - (ADV ? (hor * r2A + Wb * GsB * r2dsk) * rPc : T(0));
+      nPPh = (ADA ? X : T(0)) - (ADV ? hor * kPc + (Wb * GsB) * wc : T(0));
     }
     const T Wtp = A[12 * NTP + 1];
     {  // U cell
-      const T ZE = zf2 * (FLe + A[3 * NTP + dE1]), ZW = zf2 * (FLw + A[3 * NTP + dW1]);
+      const T FLW1 = (MC == 1) ? FLc : A[3 * NTP + dW1];   // (x-N+1) with N = 1 is the own column
+      const T psiW1 = (MC == 1) ? psi : A[11 * NTP + dW1];
+      const T ZE = zf2 * (FLe + A[3 * NTP + dE1]), ZW = zf2 * (FLw + FLW1);
       const T hor = ZE * A[1 * NTP + de] - ZW * A[1 * NTP + dw] +
                     adl2 * ((FTc + A[6 * NTP + 1]) * Gus - (FTn + A[5 * NTP + 1]) * Gun);
-      const T WuB = T(0.5) * (Wb + Wbp);
-      const T pgf = Puc * (A[11 * NTP + dE1] - A[11 * NTP + dW1]) * rdx;
-      const T fs = f0 + Guc * cota;
+      const T pgf = gU * (A[11 * NTP + dE1] - psiW1);
+      const T fs4 = f04 + Guc * cota4;
       const T vs = Vn + A[7 * NTP + 1] + Vc + A[8 * NTP + 1];
-      nPU = (ADV ? -(hor * r2A + WuB * GuB * r2dsk) * rPuc : T(0)) - (ADA ? pgf + T(0.25) * fs * vs : T(0));
+      nPU = (ADV ? -(hor * kPu + ((Wb + Wbp) * GuB) * wu) : T(0)) - (ADA ? pgf + fs4 * vs : T(0));
     }
     if (hasV) {  // V cell
-      const T ZE = zfv2 * (A[3 * NTP + dvE] + A[4 * NTP + dvE]), ZW = zfv2 * (A[3 * NTP + dvW] + A[4 * NTP + dvW]);
+      // with equal strides the V-cell faces are the divergence pairs of rows j and j+1
+      const T ZE = MC ? zfv2 * (FLe + FLse) : zfv2 * (A[3 * NTP + dvE] + A[4 * NTP + dvE]);
+      const T ZW = MC ? zfv2 * (FLw + FLsw) : zfv2 * (A[3 * NTP + dvW] + A[4 * NTP + dvW]);
       const T hor = ZE * A[2 * NTP + dve] - ZW * A[2 * NTP + dvw] +
                     adl2 * ((FTc + FTs) * Gvs - (FTn + FTc) * Gvn);
-      const T WvB = T(0.5) * (Wb + Wbs);
-      const T pgf = Pvc * (psis - psi) * rady;
-      const T cor = cn * (A[9 * NTP - 1] + A[9 * NTP]) + cs * (A[10 * NTP - 1] + A[10 * NTP]);
-      nPV = (ADV ? -(hor * r2Av + WvB * GvB * r2dsk) * rPvc : T(0)) + (ADA ? cor - pgf : T(0));
+      const T pgf = gV * (psis - psi);
+      const T cor = cn * (A[9 * NTP - 1] + fUc) + cs * (A[10 * NTP - 1] + fUs);
+      nPV = (ADV ? -(hor * kPv + ((Wb + Wbs) * GvB) * wv) : T(0)) + (ADA ? cor - pgf : T(0));
     }
     PPh = nPPh;
     PU = nPU;
@@ -551,7 +564,9 @@ __global__ void __launch_bounds__(kRowB, sizeof(T) == 4 ? AGCM_ROW_MINB : 2)
     GvB = Gvc;
     Wb = Wt;
     Wbs = Wts;
-    p_r2 = r2dsk;
+    p_wc = wc;
+    p_wu = wu;
+    p_wv = wv;
     p_ds = dsk;
     p_dsd = dsd;
     pbU = nbU;

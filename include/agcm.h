@@ -246,6 +246,20 @@ int agcm_diagnostics(const agcm_state_t* state, agcm_diag_t* out, void* stream);
  * ms_total and launches hold at least agcm_kernel_count() entries.
  */
 int agcm_profile_enable(agcm_state_t* state, int enable);
+/*
+ * agcm_set_stage_kernel — which of the library's two designs of the stage
+ * kernel runs the steps, tendencies and adjoint recomputes of every state
+ * (process-wide; results agree to rounding, both match the oracle).
+ *   0 (default): the row-segment kernel (whole latitude-row segments staged in
+ *     shared memory) when the grid's rows are 16-byte aligned (nlon % 4 == 0)
+ *     and its row segments make at least two waves of CTAs on the GPU, else
+ *     the column kernel (one thread per column, stencil read through L1);
+ *   1: always the column kernel;
+ *   2: the row-segment kernel wherever the rows allow it, on any grid size.
+ * Rows whose leap stride exceeds 63 (next to the poles on fine grids) always
+ * run the column kernel.  Other values return AGCM_EINVAL.  Host only.
+ */
+int agcm_set_stage_kernel(int choice);
 int agcm_profile_read(agcm_state_t* state, double* ms_total, int64_t* launches);
 int agcm_kernel_count(void);
 const char* agcm_kernel_name(int id);

@@ -98,6 +98,7 @@ SIGNATURES = {
     "agcm_profile_read": (_i, [_vp, _pd, ctypes.POINTER(ctypes.c_int64)]),
     "agcm_kernel_count": (_i, []),
     "agcm_kernel_name": (ctypes.c_char_p, [_i]),
+    "agcm_set_stage_kernel": (_i, [_i]),
     "agcm_tendency_static": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "agcm_ensemble_create": (_i, [ctypes.POINTER(_vp), _i, ctypes.POINTER(_vp)]),
     "agcm_ensemble_destroy": (_i, [_vp]),
@@ -130,6 +131,14 @@ def check(rc):
     if rc != AGCM_OK:
         raise AgcmError(rc, lib().agcm_last_error().decode())
     return rc
+
+
+STAGE_AUTO, STAGE_COLUMN, STAGE_ROW = 0, 1, 2
+
+
+def set_stage_kernel(choice: int) -> None:
+    """agcm_set_stage_kernel: 0 by grid (default), 1 column kernel, 2 row-segment kernel."""
+    check(lib().agcm_set_stage_kernel(int(choice)))
 
 
 def use_torch_allocator():

@@ -53,6 +53,24 @@ int fail(int code, const char* fmt, ...) {
 
 std::atomic<uint64_t> g_grid_uid{0};
 
+// Stage kernel choice (agcm_set_stage_kernel): 0 = by grid, 1 = column kernel,
+// 2 = row-segment kernel wherever the rows allow it.
+std::atomic<int> g_stage_choice{0};
+
+// Whether `items` row-segment CTAs make at least two waves on the current
+// device (three resident CTAs per SM); smaller grids run the column kernel,
+// whose one-warp blocks give more parallelism (measured on GB300: 720x360
+// rows, 2.3 waves, 0.165 against 0.185 ms per FP32 stage; 256x128, half a
+// wave, 0.072 against 0.043 ms).
+inline int rows_fill_device(long long items) {
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return items >= 2LL * 3 * nsm ? 1 : 0;
+}
+
 // Guards every grid's lazily built device tables and its count of live
 // states and ensembles, so that states may be created and destroyed from
 // several host threads.
@@ -429,6 +447,7 @@ int upload_geom(const agcm_grid* g, void** blob_out, agcm::Geom<T>* geom_out) {
   G.rowc = (const int*)(base + o_rc);
   for (int c = 0; c < 3; ++c) G.nk[c] = nk[c];
   G.nrowc = nrowc;
+  G.rowfill = rows_fill_device((long long)nk[0] + nk[1] + nk[2]);
   *blob_out = d;
   *geom_out = G;
   return AGCM_OK;
@@ -549,7 +568,9 @@ int launch_fused(const agcm::Geom<T>& G, const void* const xs[4], const double* 
     return AGCM_OK;
   };
   auto a16 = [](const void* p) { return ((uintptr_t)p & 15) == 0; };
-  bool rowpath = AGCM_ROW_KERNEL && G.nk[0] + G.nk[1] + G.nk[2] > 0 && a16(xs[0]) && a16(xs[1]) && a16(xs[2]);
+  const int choice = g_stage_choice.load(std::memory_order_relaxed);
+  bool rowpath = AGCM_ROW_KERNEL && choice != 1 && (choice == 2 || G.rowfill) && G.nk[0] + G.nk[1] + G.nk[2] > 0 &&
+                 a16(xs[0]) && a16(xs[1]) && a16(xs[2]);
   if (MODE == 2) rowpath = rowpath && a16(xb[0]) && a16(xb[1]) && a16(xb[2]);
   const size_t smem = agcm::row_smem_bytes<T>(agcm::kRowB, G.K);
   if (smem > 227 * 1024) rowpath = false;
@@ -1163,6 +1184,12 @@ int agcm_profile_read(agcm_state_t* s, double* ms_total, int64_t* launches) {
 
 int agcm_kernel_count(void) { return KID_COUNT; }
 
+int agcm_set_stage_kernel(int choice) {
+  if (choice < 0 || choice > 2) return fail(AGCM_EINVAL, "stage kernel choice must be 0, 1 or 2");
+  g_stage_choice.store(choice);
+  return AGCM_OK;
+}
+
 const char* agcm_kernel_name(int id) { return (id >= 0 && id < KID_COUNT) ? kKernelNames[id] : ""; }
 
 }  // extern "C"
@@ -1446,6 +1473,7 @@ int tendency_static(const agcm_grid* g, char* base, bool tables, const void* U, 
     std::vector<int> rk, rc;
     row_lists(g, &rk, &rc, G.nk);  // host only: counts (the lists were copied with the tables)
     G.nrowc = (int)rc.size();
+    G.rowfill = rows_fill_device((long long)G.nk[0] + G.nk[1] + G.nk[2]);
     G.rowk = (const int*)(base + kOffRowL);
     G.rowc = (const int*)(base + kOffRowL + kItemB);
   }

@@ -62,6 +62,7 @@ struct Geom {
   const int* rowk;
   const int* rowc;
   int nk[3], nrowc;
+  int rowfill;      // 1: the row-segment items fill the GPU at least four times over
 };
 
 __device__ __forceinline__ int wrapi(int i, int I) {

@@ -19,3 +19,15 @@ def cuda_ok():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     return True
+
+
+@pytest.fixture(params=["column", "row"])
+def stage_kernel(request, cuda_ok):
+    """Run a GPU test with each design of the stage kernel (the row-segment
+    kernel forced onto grids it would otherwise leave to the column kernel)."""
+    from paper_2103_10114_gb300 import agcm
+
+    agcm.build()
+    agcm.set_stage_kernel(agcm.STAGE_COLUMN if request.param == "column" else agcm.STAGE_ROW)
+    yield request.param
+    agcm.set_stage_kernel(agcm.STAGE_AUTO)

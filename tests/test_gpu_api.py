@@ -102,6 +102,48 @@ def test_profiler_counts_launches():
     s.close()
 
 
+def _row_kernel_launches(lu, lv, I):
+    """Launches of one stage on the row-segment path: one per stride class
+    present (rows whose strides Mu_j, Mv_j, Mu_{j+1} are all 1, all 3, other
+    rows with a halo of at most 64 columns) and one for the rows left to the
+    column kernel."""
+    J = len(lu)
+    classes, col = set(), False
+    for j in range(J):
+        hv = j < J - 1
+        Mu, Mv, M1 = lu[j], (lv[j] if hv else lu[j]), (lu[j + 1] if hv else lu[j])
+        H = (max(Mu, Mv if hv else 1, M1 if hv else 1) + 4) & ~3
+        if I % 4 or ((256 - 2 * H) & ~3) < 128:
+            col = True
+        elif hv and Mu == Mv == M1 and Mu in (1, 3):
+            classes.add(Mu)
+        else:
+            classes.add(0)
+    return len(classes) + (1 if col else 0)
+
+
+@pytest.mark.parametrize("grid", [(64, 32, 6), (24, 10, 3), (48, 40, 4)])
+def test_row_kernel_launches_one_per_stride_class(grid, stage_kernel):
+    """With the row-segment kernel a stage is one launch per stride class
+    present plus one for the rows it leaves to the column kernel; with the
+    column kernel, one or two (the stride-1 band)."""
+    I, J, K = grid
+    g = agcm.Grid(I, J, K)
+    lu, lv = g.leap()
+    s = agcm.State(g, agcm.AGCM_FP32)
+    s.load(inputs.random_state(I, J, K, seed=2))
+    s.profile(True)
+    s.step(2, g.dt(100.0))
+    n = s.profile_read()["k_fused_stage"][1]
+    s.profile(False)
+    if stage_kernel == "row":
+        assert n == 6 * _row_kernel_launches(lu, lv, I), (grid, n)
+    else:
+        band = [j for j in range(1, J - 2) if lu[j] == 1 and lv[j] == 1 and lu[j + 1] == 1]
+        assert n == 6 * (2 if 0 < len(band) < J else 1), (grid, n)
+    s.close()
+
+
 @pytest.mark.parametrize("leap", ["ones", "eq7", "none"])
 def test_stage_launch_count_follows_the_stride1_band(leap):
     """A stage is two launches when the grid has a run of interior rows

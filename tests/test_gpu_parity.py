@@ -74,7 +74,7 @@ def make_case(nlon, nlat, nlev, kind, extra, seed=11):
 
 
 @pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0]}x{c[1]}x{c[2]}-{c[3]}")
-def test_tendency_fp64(case):
+def test_tendency_fp64(case, stage_kernel):
     g, o, st = make_case(*case)
     s = agcm.State(g, agcm.AGCM_FP64)
     s.load(st)
@@ -85,7 +85,7 @@ def test_tendency_fp64(case):
 
 
 @pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0]}x{c[1]}x{c[2]}-{c[3]}")
-def test_one_step_fp64_and_fp32(case):
+def test_one_step_fp64_and_fp32(case, stage_kernel):
     g, o, st = make_case(*case)
     dt = g.dt(100.0)
     ref = o.step(st, dt, 1)
@@ -98,7 +98,7 @@ def test_one_step_fp64_and_fp32(case):
             assert rel_err(out[f], ref[f]) <= tol, (prec, f, rel_err(out[f], ref[f]))
 
 
-def test_config1_twenty_steps():
+def test_config1_twenty_steps(stage_kernel):
     """128 x 64 x 8 R-H wave, 20 steps at the CFL dt: FP64 parity, and the
     energy / mass drift of the GPU run equal the oracle's."""
     g, o, st = make_case(128, 64, 8, "rh4", {})
@@ -244,7 +244,7 @@ def _oracle_split(o, st, dt, msub, nsteps):
 
 @pytest.mark.parametrize("case", [(37, 23, 7, "random", {}), (128, 64, 8, "rh4", {}), (256, 128, 30, "jet", {})],
                          ids=lambda c: f"{c[0]}x{c[1]}x{c[2]}")
-def test_split_step_matches_oracle(case):
+def test_split_step_matches_oracle(case, stage_kernel):
     g, o, st = make_case(*case)
     dt, msub = g.dt_split(100.0)
     assert msub >= 2
@@ -260,7 +260,7 @@ def test_split_step_matches_oracle(case):
 
 
 @pytest.mark.parametrize("prec", [agcm.AGCM_FP64, agcm.AGCM_FP32])
-def test_zonal_translation_invariance_on_gpu(prec):
+def test_zonal_translation_invariance_on_gpu(prec, stage_kernel):
     """Shifting every field (and the terrain) by s longitudes shifts the GPU
     tendency and step by s, bit for bit: no column is treated differently,
     whether its leap partners wrap across the seam or it sits in a ragged

@@ -52,7 +52,7 @@ THERMOS = {"lapse": LAPSE, "linear": LINEAR, "full": FULL, "iso300": ISO300}
 
 @pytest.mark.parametrize("case", CASES, ids=lambda c: "x".join(map(str, c[:3])))
 @pytest.mark.parametrize("tname", list(THERMOS))
-def test_tendency_and_step(case, tname):
+def test_tendency_and_step(case, tname, stage_kernel):
     I, J, K, kind = case
     g, o, x = make(I, J, K, THERMOS[tname], kind)
     dt = g.dt(100.0)
@@ -195,7 +195,7 @@ def test_terrain_above_the_tropopause():
 
 
 @pytest.mark.parametrize("prec,tol", [(agcm.AGCM_FP64, 1e-11), (agcm.AGCM_FP32, 1e-5)])
-def test_every_option_on_a_ragged_grid(prec, tol):
+def test_every_option_on_a_ragged_grid(prec, tol, stage_kernel):
     """Non-uniform sigma, terrain, the full
     thermodynamics, split stepping and the low-latitude filter on a ragged
     38 x 23 x 7 grid (nlon even, so the two-grid removal runs; 38 is not a

@@ -111,8 +111,8 @@ int agcm_grid_destroy(agcm_grid_t* grid);
  *   delta finite; delta_c > -1; 0 <= delta_p <= 1.  NULL restores the
  *   default.  Must be called before the first state on the grid is created
  *   (the device tables are built then): AGCM_EINVAL afterwards.
- *   With delta != 0 (the nonlinear delta kappa Phi/P term) the adjoint step
- *   and ensembles return AGCM_EINVAL.
+ *   With delta != 0 (the nonlinear delta kappa Phi/P term) ensembles return
+ *   AGCM_EINVAL; the step, the tendency and the adjoint step cover it.
  */
 typedef struct agcm_thermo {
   int profile;

@@ -15,8 +15,11 @@
 //                  B = Phi / P (the level coefficient of Eq. 1 sits in the H
 //                  tables), so their adjoints are the transposed prefix /
 //                  suffix scans; D's adjoint is scattered to the fluxes.
-// The nonlinear delta kappa Phi/P term is not covered (the entry point
-// refuses it).
+// With Eq. 1's nonlinear delta kappa Phi/P term the level coefficient of
+// psi and Omega~ becomes c_k = 1 + rho_k G (G = Phi/P, the level's beta_k in
+// the tables): B_k = G c_k enters psi and -rP c_k S_k is the Omega~ tendency,
+// so the reverse column pass carries dB/dG = 1 + 2 rho_k G and the
+// derivatives of c_k.
 //   k_adj_conv     F = P^u U, G = U / P^u, ... -> adjoints of U, V, Phi and the
 //                  2-D adjoints of P, P^u, P^v, folded into the adjoint of the
 //                  mass m = pi~ + pi.
@@ -341,8 +344,10 @@ __global__ void __launch_bounds__(kAdjTileX* kAdjTileY, 5) k_adj_update(
 //   D_k  = (Fl[fE] - Fl[fW]) rdx + (sv_j Ft_j - sv_{j-1} Ft_{j-1}) rdy
 //   C    = sum_k ds_k D_k;  dpi/dt = -C
 //   W_h  = sh_h C - sum_{k<h} ds_k D_k               (h = 1..K-1)
-//   B_k  = rP Phi_k;  psi_k = sum_k' H[k][k'] B_k' + R T~_s pi / pi~
-//   X_k  = -rP (1/ds_k) sum_k' H[k'][k] ds_k' D_k'
+//   G_k  = rP Phi_k;  c_k = 1 (+ rho_k G_k with the delta kappa Phi/P term)
+//   B_k  = G_k c_k;  psi_k = sum_k' H[k][k'] B_k' + R T~_s pi / pi~
+//   S_k  = (1/ds_k) sum_k' H[k'][k] ds_k' D_k'  (stored as X),
+//   Omega~ tendency -rP c_k S_k
 //   (H carries the level coefficient beta of its source level)
 template <class T>
 __global__ void __launch_bounds__(128) k_adj_column(Geom<T> g, const T* __restrict__ Phi, ColState<T> cs,
@@ -358,7 +363,10 @@ __global__ void __launch_bounds__(128) k_adj_column(Geom<T> g, const T* __restri
   // C-bar = -ypi + sum_h sh_h Wbar_h
   double Cb = -(double)ldg(ypi + n);
   for (int h = 1; h < K; ++h) Cb += ldg(g.shd + h) * (double)ldg(a.aW + (size_t)h * plane + n);
-  // psi: Bbar_k = Hkk psibar_k + h_k sum_{k'<k} psibar_k' (prefix from the top)
+  // psi: Bbar_k = Hkk psibar_k + h_k sum_{k'<k} psibar_k' (prefix from the top);
+  // Omega~: the tendency -rP c_k S_k gives rP-bar -= ybar c' S and, with the
+  // delta kappa Phi/P term, G-bar -= ybar rP rho_k S
+  const bool nl = g.nl != 0;
   T pre = 0, psum = 0, arp = 0;
   for (int k = 0; k < K; ++k) {
     const T pb = ldg(a.aPsi + (size_t)k * plane + n);
@@ -366,11 +374,18 @@ __global__ void __launch_bounds__(128) k_adj_column(Geom<T> g, const T* __restri
     pre += pb;
     psum += pb;
     const T ph = ldg(Phi + (size_t)k * plane + n);
-    a.aPhi[(size_t)k * plane + n] = Bb * bP;
-    arp += Bb * ph;
+    const T Sx = ldg(X + (size_t)k * plane + n), yx = ldg(yPhi + (size_t)k * plane + n);
+    if (!nl) {
+      a.aPhi[(size_t)k * plane + n] = Bb * bP;
+      arp += Bb * ph - yx * Sx;
+    } else {
+      const T rho = ldg(g.rho + k), G = bP * ph;
+      const T dB = T(1) + T(2) * rho * G;      // dB/dG
+      const T Gb = Bb * dB - yx * rPc * rho * Sx;  // G-bar from psi and Omega~
+      a.aPhi[(size_t)k * plane + n] = Gb * bP;
+      arp += Gb * ph - yx * (T(1) + rho * G) * Sx;
+    }
   }
-  // X: dX_k/drP = X_k / rP
-  for (int k = 0; k < K; ++k) arp += ldg(yPhi + (size_t)k * plane + n) * ldg(X + (size_t)k * plane + n) / rPc;
   a.arPcol[n] = arp;
   a.aPiD[n] = psum * ldg(g.rt0pit + n);
   // Dbar_k = ds_k (Cb - sum_{h>k} Wbar_h) - bP ds_k (Hkk Xbar_k / ds_k + sum_{k'>k} h_k' Xbar_k' / ds_k')
@@ -383,7 +398,9 @@ __global__ void __launch_bounds__(128) k_adj_column(Geom<T> g, const T* __restri
   double SW = 0.0;
   T SX = 0;
   for (int k = K - 1; k >= 0; --k) {
-    const T xb = ldg(yPhi + (size_t)k * plane + n);
+    // Omega~ carries c_k: its D-dependence is that of -rP c_k S_k
+    T xb = ldg(yPhi + (size_t)k * plane + n);
+    if (nl) xb *= T(1) + ldg(g.rho + k) * bP * ldg(Phi + (size_t)k * plane + n);
     const T ds = ldg(g.ds + k);
     const T Db = (T)(ldg(g.dsd + k) * (Cb - SW)) - bP * (ldg(g.Hkk + k) * xb + ds * SX);
     SX += ldg(g.hk_rds + k) * xb;

@@ -1136,8 +1136,6 @@ int agcm_step_adjoint(agcm_state_t* s, const void* const lam_in[4], void* const 
   if (!s || !lam_in || !lam_out || !std::isfinite(dt)) return fail(AGCM_EINVAL, "bad argument");
   for (int f = 0; f < 4; ++f)
     if ((!lam_in[f] || !lam_out[f]) && !(f == 1 && s->nv == 0)) return fail(AGCM_EINVAL, "null adjoint buffer %d", f);
-  if (s->grid->beta2 != 0.0 && s->grid->th.delta != 0.0)
-    return fail(AGCM_EINVAL, "the adjoint step does not cover the nonlinear delta kappa Phi/P term");
   cudaStream_t st = as_stream(stream);
   return s->prec == AGCM_FP64 ? adjoint_step<double>(s, lam_in, lam_out, dt, st)
                               : adjoint_step<float>(s, lam_in, lam_out, dt, st);

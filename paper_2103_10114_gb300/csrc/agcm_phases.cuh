@@ -68,9 +68,11 @@ __device__ __forceinline__ T divergence(const Geom<T>& g, const T* __restrict__ 
   return d + mer * g.rdy[j];
 }
 
-// Phase B outputs.  W: (K+1)*J*I half-level mass fluxes; X: Omega~ tendency;
-// psi: hydrostatic potential; pi_out = pi_base - c*dt*C (or -C when
-// pi_base == nullptr and c*dt = 1).
+// Phase B outputs.  W: (K+1)*J*I half-level mass fluxes; X: the factor
+// S_k = Hkk_k D_k + hkr_k Q_k of the Omega~ tendency -rP c_k S_k (Q_k the
+// divergence integrated from the top; c_k = 1, or 1 + rho_k Phi_k / P with
+// Eq. 1's delta kappa Phi/P term); psi: hydrostatic potential;
+// pi_out = pi_base - c*dt*C (or -C when pi_base == nullptr and c*dt = 1).
 template <class T>
 __global__ void __launch_bounds__(128) k_column(Geom<T> g, const T* __restrict__ U, const T* __restrict__ V,
                                                 const T* __restrict__ Phi, const T* __restrict__ pi,
@@ -88,22 +90,24 @@ __global__ void __launch_bounds__(128) k_column(Geom<T> g, const T* __restrict__
   if (Cout) Cout[n] = C;
   const double pb = pi_base ? (double)pi_base[n] : 0.0;
   pi_out[n] = (T)(pb - cdt * C);
-  // pass 2: prefix sum from the top -> W at half levels and the Omega~ term
+  // pass 2: prefix sum from the top -> W at half levels and the Omega~ factor
   const T bP = cs.rP[n];  // the level coefficient sits in the H tables
   double Q = 0.0;
   W[n] = T(0);
   for (int k = 0; k < K; ++k) {
     const T D = divergence(g, U, V, cs.Pu, cs.Pv, k, j, i);
     if (k > 0) W[(size_t)k * plane + n] = (T)(g.shd[k] * C - Q);
-    X[(size_t)k * plane + n] = -bP * (g.Hkk[k] * D + g.hk_rds[k] * (T)Q);
+    X[(size_t)k * plane + n] = g.Hkk[k] * D + g.hk_rds[k] * (T)Q;
     Q += g.dsd[k] * (double)D;
   }
   W[(size_t)K * plane + n] = T(0);
-  // pass 3: suffix sum from the surface -> phi' + R T~_s pi / pi~
+  // pass 3: suffix sum from the surface -> phi' + R T~_s pi / pi~, with
+  // B = Phi/P, times 1 + rho_k Phi/P under the delta kappa Phi/P term
   const T ps = g.rt0pit[n] * pi[n];
   T S = T(0);
   for (int k = K - 1; k >= 0; --k) {
-    const T B = bP * Phi[(size_t)k * plane + n];
+    T B = bP * Phi[(size_t)k * plane + n];
+    if (g.nl) B *= T(1) + g.rho[k] * B;
     psi[(size_t)k * plane + n] = g.Hkk[k] * B + S + ps;
     S += g.hk[k] * B;
   }

@@ -279,10 +279,13 @@ const char* agcm_kernel_name(int id);
  * e.g. when other work occupies the GPU).  The launch can be captured in a
  * CUDA graph once a first call has uploaded the dt values (nsteps = 0 only
  * prepares: it uploads dt and the members' vertical means without stepping).
- * agcm_ensemble_configure sets the launch shape (warps per block: 1; blocks
- * per SM, 0 = as many as fit); agcm_ensemble_tile sets the row tile of a
- * work item (1, 2 or 4 consecutive rows of 32 columns, taken by one warp in
- * order); an autotuner picks both (ensemble.py).  Set both before capturing
+ * agcm_ensemble_configure sets the launch shape: warps per block 1 (one-warp
+ * blocks running the column body on items of 32 columns) or 8 (256-thread
+ * blocks running the row-segment body on (member, row segment) items, the
+ * rows it leaves on the column body), and blocks per SM (0 = as many as
+ * fit); agcm_ensemble_tile sets the row tile of a one-warp work item (1, 2 or
+ * 4 consecutive rows of 32 columns, taken by one warp in order); an
+ * autotuner picks among them (ensemble.py).  Set both before capturing
  * a graph: a replay keeps the shape it was captured with.
  * agcm_ensemble_set_timeout: barrier timeout in seconds; test_missing_blocks
  * > 0 makes every barrier wait for blocks that do not exist, to exercise the

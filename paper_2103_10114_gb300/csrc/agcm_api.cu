@@ -1544,6 +1544,11 @@ struct agcm_ensemble {
   double timeout_s = 1.0;
   int test_missing = 0;
   bool desc_dirty = true;
+  // work items of the row-segment persistent launch (warps_per_block = 8)
+  std::vector<int> host_items;   // int2 pairs
+  void* d_items = nullptr;
+  int nitems_rows = 0;
+  size_t rows_smem = 0;          // dynamic shared memory of that launch
   std::vector<double> last_dt;
   Profiler prof;
 };
@@ -1569,6 +1574,27 @@ void fill_desc(agcm_ensemble* e) {
     begin += d[m].nbx * ((s->grid->J + e->rows_per_item - 1) / e->rows_per_item);
   }
   e->nitems = begin;
+  // row-segment persistent launch: every member's row-segment items (any
+  // stride class), then 256-column chunks of the rows left to the column body
+  e->host_items.clear();
+  e->rows_smem = 0;
+  for (size_t m = 0; m < e->members.size(); ++m) {
+    const agcm_grid* g = e->members[m]->grid;
+    std::vector<int> rk, rc;
+    int nk[3];
+    row_lists(g, &rk, &rc, nk);
+    for (int it : rk) {
+      e->host_items.push_back((int)m);
+      e->host_items.push_back(it);
+    }
+    for (int j : rc)
+      for (int c = 0; c * agcm::kRowB < g->I; ++c) {
+        e->host_items.push_back((int)m | (1 << 16));
+        e->host_items.push_back(j << 8 | c);
+      }
+    e->rows_smem = std::max(e->rows_smem, agcm::row_smem_bytes<T>(agcm::kRowB, g->K));
+  }
+  e->nitems_rows = (int)(e->host_items.size() / 2);
 }
 
 template <class T>
@@ -1595,6 +1621,29 @@ int ensemble_step(agcm_ensemble* e, int nsteps, const double* dt, cudaStream_t s
   CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   CUDA_TRY(cudaDeviceGetAttribute(&clock_khz, cudaDevAttrClockRate, dev));
   const int threads = 32 * e->warps_per_block;
+  if (e->warps_per_block == 8) {  // the row-segment persistent launch
+    auto kr = agcm::k_ensemble_rows<T>;
+    if (e->rows_smem > 227 * 1024) return fail(AGCM_EINVAL, "ensemble member with too many levels for the row launch");
+    CUDA_TRY(cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)e->rows_smem));
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kr, agcm::kRowB, e->rows_smem));
+    if (occ < 1) return fail(AGCM_EINVAL, "row-segment ensemble kernel does not fit");
+    const int per_sm = e->blocks_per_sm > 0 ? std::min(e->blocks_per_sm, occ) : occ;
+    const unsigned grid = (unsigned)(per_sm * nsm);
+    const long long limit = (long long)(e->timeout_s * (double)clock_khz * 1000.0);
+    const size_t sync_bytes = sizeof(agcm::EnsSync) + sizeof(unsigned) * (size_t)e->queue_cap * 3;
+    for (int done = 0; done < nsteps; done += e->queue_cap) {
+      const int chunk = std::min(e->queue_cap, nsteps - done);
+      CUDA_TRY(cudaMemsetAsync(e->d_sync, 0, sync_bytes, st));
+      e->prof.begin(KID_ENSEMBLE, st);
+      kr<<<grid, agcm::kRowB, e->rows_smem, st>>>((const agcm::EnsMember<T>*)e->d_desc, (const int2*)e->d_items,
+                                                 e->nitems_rows, chunk, e->d_sync, grid + (unsigned)e->test_missing,
+                                                 limit);
+      e->prof.end(st);
+      CUDA_TRY(cudaGetLastError());
+    }
+    for (agcm_state* s : e->members) s->bar_valid = true;
+    return AGCM_OK;
+  }
   auto kern = e->rows_per_item == 4 ? agcm::k_ensemble<T, 4>
                                     : (e->rows_per_item == 2 ? agcm::k_ensemble<T, 2> : agcm::k_ensemble<T, 1>);
   CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, 0));
@@ -1647,10 +1696,18 @@ int agcm_ensemble_create(agcm_state_t* const* members, int n, agcm_ensemble_t** 
     fill_desc<float>(e);
   e->queue_cap = 1024;
   e->d_desc = dev_alloc(e->host_desc.size());
+  e->d_items = dev_alloc(std::max<size_t>(e->host_items.size(), 2) * sizeof(int));
+  if (e->d_items && !e->host_items.empty() &&
+      cudaMemcpy(e->d_items, e->host_items.data(), e->host_items.size() * sizeof(int), cudaMemcpyHostToDevice) !=
+          cudaSuccess) {
+    dev_free(e->d_items);
+    e->d_items = nullptr;
+  }
   e->d_sync = (agcm::EnsSync*)dev_alloc(sizeof(agcm::EnsSync) + sizeof(unsigned) * (size_t)e->queue_cap * 3);
-  if (!e->d_desc || !e->d_sync) {
+  if (!e->d_desc || !e->d_sync || !e->d_items) {
     dev_free(e->d_desc);
     dev_free(e->d_sync);
+    dev_free(e->d_items);
     delete e;
     return fail(AGCM_ENOMEM, "device allocation for the ensemble failed");
   }
@@ -1667,6 +1724,7 @@ int agcm_ensemble_destroy(agcm_ensemble_t* e) {
   cudaDeviceSynchronize();
   dev_free(e->d_desc);
   dev_free(e->d_sync);
+  dev_free(e->d_items);
   {
     std::lock_guard<std::mutex> lk(g_grid_mu);
     for (agcm_state* s : e->members) const_cast<agcm_grid*>(s->grid)->refs--;
@@ -1676,8 +1734,8 @@ int agcm_ensemble_destroy(agcm_ensemble_t* e) {
 }
 
 int agcm_ensemble_configure(agcm_ensemble_t* e, int warps_per_block, int blocks_per_sm) {
-  if (!e || warps_per_block != 1 || blocks_per_sm < 0)
-    return fail(AGCM_EINVAL, "warps_per_block must be 1 and blocks_per_sm >= 0");
+  if (!e || (warps_per_block != 1 && warps_per_block != 8) || blocks_per_sm < 0)
+    return fail(AGCM_EINVAL, "warps_per_block must be 1 or 8 and blocks_per_sm >= 0");
   e->warps_per_block = warps_per_block;
   e->blocks_per_sm = blocks_per_sm;
   return AGCM_OK;

@@ -15,6 +15,7 @@
 #pragma once
 #include "agcm_common.cuh"
 #include "agcm_fused.cuh"
+#include "agcm_row.cuh"
 
 namespace agcm {
 
@@ -135,6 +136,83 @@ __global__ void __launch_bounds__(32, sizeof(T) == 4 ? AGCM_ENS_MINB : 8)
           }
         }
       }
+      __threadfence();
+      if (!ens_barrier(sy, expected_blocks, limit)) return;
+    }
+  }
+}
+
+// The column body for the few rows the row-segment body leaves, out of line
+// so that its registers do not burden the row-segment body.
+template <class T>
+__device__ __noinline__ void ens_column_item(const EnsMember<T>& e, int i, int j, int a, int b, T c) {
+  fused_column<T, 2>(e.g, i, j, e.x[a][0], e.x[a][1], e.x[a][2], e.x[a][3], e.ubar[a], e.vbar[a], e.x[0][0],
+                     e.x[0][1], e.x[0][2], e.x[0][3], e.x[b][0], e.x[b][1], e.x[b][2], e.x[b][3], e.ubar[b],
+                     e.vbar[b], e.ubar[0], e.vbar[0], c);
+}
+
+// The row-segment form of the persistent launch: CTAs of kRowB threads (the
+// single-state row-segment kernel's shape, AGCM_ROW_MINB resident per SM)
+// pull work items of every member from the stage's queue:
+//   kind 0: (member, row j, segment) — the row-segment body, stride class 0
+//           (any strides), with the member's tables from its descriptor;
+//   kind 1: (member, row j, 256-column chunk) — rows the row-segment body
+//           leaves (strides above 63, rows not 16-byte aligned): each warp runs
+//           the column body on 32 columns of the chunk.
+// Items are int2 {member | kind << 16, j << 8 | segment-or-chunk}.  Every
+// stage uses x_n as its base (stage 1 reads it as input and base), the three
+// stages of a step as in agcm_step; a bounded grid barrier separates them.
+template <class T>
+__global__ void __launch_bounds__(kRowB, sizeof(T) == 4 ? AGCM_ROW_MINB : 2)
+    k_ensemble_rows(const EnsMember<T>* __restrict__ mem, const int2* __restrict__ items, int nitems, int nsteps,
+                    EnsSync* sy, unsigned expected_blocks, long long limit) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  // the current member's descriptor, copied to shared memory when it changes
+  __shared__ __align__(16) unsigned long long sdesc[(sizeof(EnsMember<T>) + 7) / 8];
+  __shared__ int s_item;
+  // the stage's arguments for the row-segment body, kept in shared memory so
+  // that the body reads its pointers from there rather than holding them
+  __shared__ __align__(16) unsigned long long sargs[(sizeof(RowArgs<T>) + 7) / 8];
+  RowArgs<T>& ra = *reinterpret_cast<RowArgs<T>*>(sargs);
+  const EnsMember<T>& e = *reinterpret_cast<const EnsMember<T>*>(sdesc);
+  const int t = threadIdx.x;
+  int cur = -1;
+  bool fresh = true;  // the row-segment body's mbarriers are not initialised yet
+  for (int step = 0; step < nsteps; ++step) {
+    for (int stage = 0; stage < 3; ++stage) {
+      unsigned int* q = &sy->queue[step * 3 + stage];
+      while (true) {
+        __syncthreads();  // every thread is past the previous item
+        if (t == 0) s_item = (int)atomicAdd(q, 1u);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= nitems) break;
+        const int2 w = items[it];
+        const int m = w.x & 0xffff, kind = w.x >> 16;
+        // stage 1: x_n -> x1 (dt/2); stage 2: x1 -> x2 (dt/2); stage 3: x2 -> x_n (dt)
+        const int a = stage, b = stage == 0 ? 1 : (stage == 1 ? 2 : 0);
+        if (m != cur) {
+          const unsigned long long* src = reinterpret_cast<const unsigned long long*>(mem + m);
+          for (int q2 = t; q2 < (int)((sizeof(EnsMember<T>) + 7) / 8); q2 += blockDim.x) sdesc[q2] = src[q2];
+          __syncthreads();
+          if (t == 0)
+            ra = RowArgs<T>{e.x[a][0], e.x[a][1], e.x[a][2], e.x[a][3], e.ubar[a], e.vbar[a],
+                            e.x[0][0], e.x[0][1], e.x[0][2], e.x[0][3], e.x[b][0], e.x[b][1], e.x[b][2], e.x[b][3],
+                            e.ubar[b], e.vbar[b], e.ubar[0], e.vbar[0],
+                            stage == 2 ? e.dt : T(0.5) * e.dt, nullptr, &sy->status};
+          __syncthreads();
+          cur = m;
+        }
+        const T c = stage == 2 ? e.dt : T(0.5) * e.dt;
+        if (kind == 0) {
+          row_segment<T, 2, 3, false, 0>(e.g, ra, w.y >> 8, w.y & 255, smem, fresh);
+          fresh = false;
+        } else {
+          const int i = (w.y & 255) * kRowB + t;
+          if (i < e.g.I) ens_column_item<T>(e, i, w.y >> 8, a, b, c);
+        }
+      }
+      cur = -1;  // the next stage rebuilds the member's arguments
       __threadfence();
       if (!ens_barrier(sy, expected_blocks, limit)) return;
     }

@@ -190,15 +190,19 @@ __host__ __device__ constexpr size_t row_smem_bytes(int NTP, int K) {
 // is scaled by 1 + rho_k Phi/P).  MC > 0: every row of the launch has
 // Mu_j = Mv_j = Mu_{j+1} = MC, so the partner offsets are compile-time
 // constants; MC = 0: any strides.
+//
+// row_segment runs one work item (row j, segment seg) with the CTA's dynamic
+// shared memory `smem`; fresh = false when an earlier item of the same CTA
+// left its mbarriers initialised (a persistent CTA running item after item,
+// with every thread of the CTA past the earlier item).  A `return` only ends
+// the item for the threads that take it.
 template <class T, int MODE, int TERMS, bool NL, int MC>
-__global__ void __launch_bounds__(kRowB, sizeof(T) == 4 ? AGCM_ROW_MINB : 2)
-    k_row_stage(const Geom<T> g, const RowArgs<T> a) {
+__device__ __forceinline__ void row_segment(const Geom<T>& g, const RowArgs<T>& a, const int j, const int seg,
+                                            unsigned char* smem, const bool fresh) {
   constexpr int R = RowCfg<T>::R;
   constexpr bool ADV = (TERMS & 1) != 0, ADA = (TERMS & 2) != 0;
   constexpr bool kInc = sizeof(T) == 4 && MODE != 0;
   const int I = g.I, J = g.J, K = g.K;
-  const int item = a.rows[blockIdx.x];  // row j and segment of this CTA
-  const int j = item >> 8, seg = item & 255;
   const bool hasV = MC > 0 || j < J - 1;  // V row j (and scalar row j+1) exist; the classes hold no last row
   const int Mu = MC ? MC : g.Mu[j];
   const int Mv = MC ? MC : (hasV ? g.Mv[j] : 1);
@@ -222,7 +226,6 @@ __global__ void __launch_bounds__(kRowB, sizeof(T) == 4 ? AGCM_ROW_MINB : 2)
   // shared memory: ring mbarriers, abort flag, descriptor count; the copy
   // descriptors; the ring of staged raw rows; two buffers of the published
   // arrays; the P^u rows j and j+1; the level tables
-  extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 8 * R);
   int* s_ndesc = reinterpret_cast<int*>(smem + 8 * R + 4);
@@ -250,6 +253,9 @@ __global__ void __launch_bounds__(kRowB, sizeof(T) == 4 ? AGCM_ROW_MINB : 2)
   }
   const unsigned ring_s = smem_addr(ring);
   if (t == 0) {
+    if (!fresh)
+      for (int s = 0; s < R; ++s)
+        asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar + s)) : "memory");
     for (int s = 0; s < R; ++s) mbar_init(bar + s, 1);
     *abort_flag = 0;
     // one descriptor per piece of every staged row that exists: q = 0..2 U
@@ -603,6 +609,15 @@ __global__ void __launch_bounds__(kRowB, sizeof(T) == 4 ? AGCM_ROW_MINB : 2)
     while (clock64() - t1 < 2000000LL) {
     }
   }
+}
+
+// One work item per CTA: a.rows[blockIdx.x] = row j << 8 | segment.
+template <class T, int MODE, int TERMS, bool NL, int MC>
+__global__ void __launch_bounds__(kRowB, sizeof(T) == 4 ? AGCM_ROW_MINB : 2)
+    k_row_stage(const Geom<T> g, const RowArgs<T> a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int item = a.rows[blockIdx.x];
+  row_segment<T, MODE, TERMS, NL, MC>(g, a, item >> 8, item & 255, smem, true);
 }
 
 }  // namespace agcm

@@ -3,11 +3,12 @@ an autotuner for its launch shape, and CUDA-graph replay.
 
 Two ways to advance the members, both captured whole in one CUDA graph:
 
-* "persistent": one launch of the ensemble kernel (agcm_ensemble_step); its
-  launch shape (one-warp blocks, how many resident per SM) and the row tile of
-  a work item (32 columns of 1, 2 or 4 consecutive rows, taken in order by one
-  warp) decide how the work spreads over the SMs and how many warps hide each
-  other's memory latency;
+* "persistent": one launch of the ensemble kernel (agcm_ensemble_step), in
+  one of two forms: one-warp blocks running the column body on items of 32
+  columns of 1, 2 or 4 consecutive rows (its launch shape: how many blocks are
+  resident per SM, and the row tile); or 256-thread blocks (warps_per_block
+  8) running the row-segment body on (member, row segment) items, with the
+  rows near the poles on the column body;
 * "streams": each member stepped by the single-state kernel (agcm_step) with
   the members spread round-robin over N CUDA streams, so small members run
   side by side.  The single-state kernel reads its grid tables from the launch
@@ -113,6 +114,7 @@ class Ensemble:
             return _TUNE_CACHE[key], {}
         if candidates is None:
             candidates = [(1, b, r) for r in (1, 2, 4) for b in (0, 8, 16)]
+            candidates += [(8, b, 1) for b in (0, 2)]
             candidates += [("streams", n) for n in (4, 8, 16)]
         saved = [s.store() for s in self.states]
         times = {}

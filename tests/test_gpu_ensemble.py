@@ -33,14 +33,18 @@ def np_state(s):
     return {f: v.double().cpu().numpy() for f, v in s.store().items()}
 
 
-@pytest.mark.parametrize("prec,rows", [(agcm.AGCM_FP32, 1), (agcm.AGCM_FP64, 1), (agcm.AGCM_FP32, 2),
-                                       (agcm.AGCM_FP64, 4)])
-def test_member_equals_single_run(prec, rows):
+@pytest.mark.parametrize("prec,shape", [(agcm.AGCM_FP32, (1, 0, 1)), (agcm.AGCM_FP64, (1, 0, 1)),
+                                        (agcm.AGCM_FP32, (1, 0, 2)), (agcm.AGCM_FP64, (1, 0, 4)),
+                                        (agcm.AGCM_FP32, (8, 0, 1)), (agcm.AGCM_FP64, (8, 0, 1)),
+                                        (agcm.AGCM_FP32, (8, 1, 1))])
+def test_member_equals_single_run(prec, shape):
     """Every member after three ensemble steps equals its own run; row tiles
-    of 2 and 4 rows leave ragged last tiles on the member grids (nlat 23)."""
+    of 2 and 4 rows leave ragged last tiles on the member grids (nlat 23);
+    the 256-thread launch runs the row-segment body (the 37-column member,
+    whose rows are not 16-byte aligned, on the column body)."""
     mem = members(prec)
     ens = Ensemble([m[1] for m in mem])
-    ens.configure(1, 0, rows)
+    ens.configure(*shape)
     dts = [m[3] for m in mem]
     ens.step(3, dts)
     ens.status()
@@ -59,11 +63,13 @@ def test_member_equals_single_run(prec, rows):
     ens.close()
 
 
-def test_graph_replay_equals_eager():
+@pytest.mark.parametrize("shape", [(1, 0, 1), (8, 0, 1)])
+def test_graph_replay_equals_eager(shape):
     import torch
 
     mem = members(agcm.AGCM_FP32)
     ens = Ensemble([m[1] for m in mem])
+    ens.configure(*shape)
     dts = [m[3] for m in mem]
     x0 = [m[1].store() for m in mem]
     graph = ens.capture(2, dts)
@@ -84,9 +90,11 @@ def test_graph_replay_equals_eager():
     ens.close()
 
 
-def test_barrier_timeout_is_reported_and_context_survives():
+@pytest.mark.parametrize("shape", [(1, 0, 1), (8, 0, 1)])
+def test_barrier_timeout_is_reported_and_context_survives(shape):
     mem = members(agcm.AGCM_FP32, mix=[(64, 32, 6), (48, 24, 5)])
     ens = Ensemble([m[1] for m in mem])
+    ens.configure(*shape)
     dts = [m[3] for m in mem]
     x0 = [m[1].store() for m in mem]
     ens.set_timeout(0.2, test_missing_blocks=1)  # every barrier waits for a block that never comes

@@ -306,10 +306,16 @@ __device__ __forceinline__ void row_segment(const Geom<T>& g, const RowArgs<T>& 
   const int warp = __shfl_sync(0xffffffffu, t >> 5, 0);
   const int ndesc = *s_ndesc;
   const unsigned txb = *s_tx;
+  // a warp's first two descriptors are read once, for every level
+  RowDesc d0{nullptr, 0, 0, 0}, d1{nullptr, 0, 0, 0};
+  if (warp < ndesc) d0 = desc[warp];
+  if (warp + nw < ndesc) d1 = desc[warp + nw];
   auto issue_level = [&](int kk, int s) {
     if (warp == 0) mbar_expect_tx_warp(bar + s, txb);
     const unsigned base = ring_s + (unsigned)(s * kRowRaw * NTP * sizeof(T));
-    for (int d = warp; d < ndesc; d += nw) {
+    if (d0.bytes) bulk_copy_g2s_warp(base + d0.dst, d0.src0 + (unsigned long long)kk * d0.plane_bytes, d0.bytes, bar + s);
+    if (d1.bytes) bulk_copy_g2s_warp(base + d1.dst, d1.src0 + (unsigned long long)kk * d1.plane_bytes, d1.bytes, bar + s);
+    for (int d = warp + 2 * nw; d < ndesc; d += nw) {  // segments of fewer than six warps
       const RowDesc e = desc[d];
       bulk_copy_g2s_warp(base + e.dst, e.src0 + (unsigned long long)kk * e.plane_bytes, e.bytes, bar + s);
     }

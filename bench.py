@@ -41,27 +41,30 @@ BYTES_PER_POINT_STEP = {4: 96, 8: 192}  # 24 words: stages read/write 6 + 9 + 9 
 # DRAM traffic of the dominant kernel from an ncu capture of this workload,
 # valid only while the kernel source is the one that was captured.
 NCU_TRAFFIC = {
-    # kernel name: (sha1 of csrc/agcm_fused.cuh at capture time, bytes per stage
-    # summed over the stage's launches)
-    "k_fused_stage": ("a158a453d601b41695444c2c22bff95e79ec9cf7", 1060219904),
+    # kernel bracket name: (sha1 of the stage-kernel sources at capture time,
+    # DRAM bytes per stage summed over the stage's launches)
+    "k_fused_stage": ("5157b1b93784addc97816fad2c174e916c5ffcfd", 957000000),
 }
 
-# Instruction counters of the dominant kernel (ncu, 720x360x30 FP32, the launches
-# of each stage summed, averaged over the three stages), valid while the kernel
-# source is the one that was captured: FP32 flops per point and stage
-# (fadd + fmul + 2 ffma), thread instructions per point, warp instructions
-# issued per point.
+# Instruction counters of the dominant kernel (ncu per-opcode counts, this
+# workload, a later stage's launches weighted by the points of their rows),
+# valid while the kernel source is the one that was captured: FP32 flops per
+# point and stage (fadd + fmul + 2 ffma), thread instructions per point, warp
+# instructions issued per point.
 NCU_OPS = {
-    "k_fused_stage": ("a158a453d601b41695444c2c22bff95e79ec9cf7", 218.0, 460.1, 14.70),
+    "k_fused_stage": ("5157b1b93784addc97816fad2c174e916c5ffcfd", 182.9, 358.9, 11.22),
 }
 
 
 def kernel_source_hash():
+    """sha1 of the stage kernels' sources (the row-segment and column kernels)."""
     import hashlib
 
-    p = os.path.join(ROOT, "paper_2103_10114_gb300", "csrc", "agcm_fused.cuh")
-    with open(p, "rb") as f:
-        return hashlib.sha1(f.read()).hexdigest()
+    h = hashlib.sha1()
+    for name in ("agcm_row.cuh", "agcm_fused.cuh", "agcm_common.cuh"):
+        with open(os.path.join(ROOT, "paper_2103_10114_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 
 
 def peaks():
@@ -242,7 +245,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
-    ap.add_argument("--only", choices=["adjoint", "ensemble", "fp64", "fp32_720", "split", "filter", "thermo", "gradient"],
+    ap.add_argument("--only", choices=["adjoint", "ensemble", "fp64", "fp32", "fp32_720", "split", "filter", "thermo",
+                                       "gradient"],
                     help="measure one form alone and print its JSON (for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -346,7 +350,7 @@ def main():
                    "fp32_tflops": fp32, "fp32_peak_tflops": fp32_peak, "fp32_frac": fp32 / fp32_peak,
                    "warp_inst_per_point_stage": orec[3], "issue_frac": issue / issue_peak,
                    "peak_note": f"{nsm} SMs x 128 FP32 lanes x 2 x {fmax:.0f} MHz; issue: 4 warp-inst/SM/cycle",
-                   "source": f"ncu instruction counters, 720x360x30 FP32, source sha1 {orec[0][:12]}"}
+                   "source": f"ncu per-opcode counts, this workload, source sha1 {orec[0][:12]}"}
     launches = sum(n for _, n in prof.values())
     line = {
         "metric": "grid-point-steps/s", "value": value, "unit": "gp-steps/s", "n_gpus": world,
@@ -455,11 +459,11 @@ def run_only(form):
         out = measure_thermo(agcm, inputs, torch, steps=3)
     elif form == "gradient":
         out = measure_gradient(agcm, inputs, torch)
-    else:  # fp64: the plain FP64 step at the bench size; fp32_720: FP32 at 720x360x30
-        I, J, K = WORKLOAD if form == "fp64" else (720, 360, 30)
+    else:  # fp64 / fp32: the plain FP64 / FP32 step at the bench size; fp32_720: FP32 at 720x360x30
+        I, J, K = (720, 360, 30) if form == "fp32_720" else WORKLOAD
         st = inputs.baroclinic_jet(I, J, K, seed=6, noise=1e-2, terrain_seed=2)
         g = agcm.Grid(I, J, K, phis=st["phis"])
-        s = agcm.State(g, agcm.AGCM_FP64 if form == "fp64" else agcm.AGCM_FP32)
+        s = agcm.State(g, agcm.AGCM_FP64 if form == "fp64" else agcm.AGCM_FP32)  # noqa: E501
         s.load(st)
         s.step(1, g.dt(100.0))
         ms = _time(torch, lambda: s.step(2, g.dt(100.0)), 1) / 2

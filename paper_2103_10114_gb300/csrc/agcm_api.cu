@@ -154,20 +154,19 @@ struct agcm_grid {
 // Kernel ids for the per-kernel event timing.
 enum KernelId : int {
   KID_COLSTATE = 0,
-  KID_COLUMN,
   KID_VSUM,
   KID_FUSED,
   KID_DIAG,
-  KID_ADJ_UPDATE,
-  KID_ADJ_COLUMN,
+  KID_ADJ_COL,
+  KID_ADJ_GATHER,
   KID_ADJ_COLSTATE,
   KID_ENSEMBLE,
   KID_FILTER,
   KID_COUNT
 };
 static const char* const kKernelNames[KID_COUNT] = {
-    "k_colstate", "k_column", "k_vsum", "k_fused_stage", "k_diag",
-    "k_adj_update", "k_adj_column", "k_adj_colstate", "k_ensemble", "k_filter"};
+    "k_colstate", "k_vsum", "k_fused_stage", "k_diag",
+    "k_adj_col", "k_adj_gather", "k_adj_colstate", "k_ensemble", "k_filter"};
 
 struct Profiler {
   bool on = false;
@@ -227,10 +226,9 @@ struct agcm_state {
   // prognostic x_n and the stage states x1, x2 (U, V, Phi, pi packed)
   void* x[3][4] = {};
   // adjoint forward-recompute scratch (allocated with the adjoint workspace):
-  // P, rP, Pu, rPu, Pv, rPv (2-D), W ((K+1) planes), X, psi
+  // P, rP, Pu, rPu, Pv, rPv (2-D), W ((K+1) planes), psi
   void* col[6] = {};
   void* W = nullptr;
-  void* X = nullptr;
   void* psi = nullptr;
   // FP64 vertical means sum_k dsigma U_k and V_k of x[0..2] (J*I each), the
   // input of the fused stage kernel's column integral; bar_valid for x[0]
@@ -247,10 +245,15 @@ struct agcm_state {
   std::vector<void*> owned;
   // adjoint workspace (allocated on the first agcm_step_adjoint call)
   bool adj_ready = false;
-  void* adj3[9] = {};   // aU aFl aGu aGs aPsi aPhi tRP tRPu tPu   (K*J*I)
-  void* adjv[5] = {};   // aV aFt aGv tRPv tPv                      (K*(J-1)*I)
-  void* adjW = nullptr; // aW                                       ((K+1)*J*I)
-  void* adj2[6] = {};   // arPcol aPiD mub mvb mcb pi_scratch       (J*I)
+  void* adj3[2] = {};   // Db aPhi                                  (K*J*I)
+  void* adj2[5] = {};   // arPcol aPiD mub mvb mcb                  (J*I)
+  // rows of the adjoint gather: row-segment items (j << 8 | segment) of
+  // k_adj_rows, and the rows left to k_adj_gather
+  int* adj_items = nullptr;
+  int n_adj_items = 0;
+  int* adj_rows = nullptr;
+  int n_adj_rows = 0;
+  void* adj_part = nullptr;  // level-chunk partial sums of those rows (3 * chunks * rows * I)
   void* mu[2][4] = {};  // stage adjoints mu2, mu1
 };
 
@@ -1136,6 +1139,9 @@ int agcm_step_adjoint(agcm_state_t* s, const void* const lam_in[4], void* const 
   if (!s || !lam_in || !lam_out || !std::isfinite(dt)) return fail(AGCM_EINVAL, "bad argument");
   for (int f = 0; f < 4; ++f)
     if ((!lam_in[f] || !lam_out[f]) && !(f == 1 && s->nv == 0)) return fail(AGCM_EINVAL, "null adjoint buffer %d", f);
+  for (int f = 0; f < 4; ++f)
+    for (int q = 0; q < 4; ++q)
+      if (lam_in[f] && lam_in[f] == lam_out[q]) return fail(AGCM_EINVAL, "lam_in and lam_out alias (buffer %d)", f);
   cudaStream_t st = as_stream(stream);
   return s->prec == AGCM_FP64 ? adjoint_step<double>(s, lam_in, lam_out, dt, st)
                               : adjoint_step<float>(s, lam_in, lam_out, dt, st);
@@ -1209,12 +1215,37 @@ int ensure_adj(agcm_state* s) {
   // forward recompute (phases A, B) at the stage states
   for (auto& p : s->col) p = get(n2);
   s->W = get(nw);
-  s->X = get(n3);
   s->psi = get(n3);
   for (auto& p : s->adj3) p = get(n3);
-  for (auto& p : s->adjv) p = get(nv);
-  s->adjW = get(nw);
   for (auto& p : s->adj2) p = get(n2);
+  // rows whose adjoint halo fits a row segment go to k_adj_rows
+  const agcm_grid* g = s->grid;
+  std::vector<int> items, rows;
+  for (int j = 0; j < g->J; ++j) {
+    const int H = agcm::adj_row_halo(g->Mu[j], j < g->J - 1 ? g->Mv[j] : 0, j > 0 ? g->Mv[j - 1] : 0);
+    int nseg = 0, S = 0;
+    if (H <= agcm::kAdjRowMaxH && H < g->I) agcm::adj_row_segments(g->I, H, &nseg, &S);
+    if (nseg > 0 && nseg <= 256) {
+      for (int q = 0; q < nseg; ++q)
+        if (q * S < g->I) items.push_back(j << 8 | q);
+    } else {
+      rows.push_back(j);
+    }
+  }
+  auto put_ints = [&](const std::vector<int>& v) -> int* {
+    if (v.empty()) return nullptr;
+    int* d = (int*)get(v.size() * sizeof(int));
+    if (d && cudaMemcpy(d, v.data(), v.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) ok = false;
+    return d;
+  };
+  s->adj_items = put_ints(items);
+  s->n_adj_items = (int)items.size();
+  s->adj_rows = put_ints(rows);
+  s->n_adj_rows = (int)rows.size();
+  if (!rows.empty()) {
+    const size_t nch = (size_t)(g->K + agcm::kAdjLevChunk - 1) / agcm::kAdjLevChunk;
+    s->adj_part = get(3 * nch * rows.size() * g->I * e);
+  }
   for (int c = 0; c < 2; ++c) {
     s->mu[c][0] = get(n3);
     s->mu[c][1] = get(nv);
@@ -1227,52 +1258,64 @@ int ensure_adj(agcm_state* s) {
 }
 
 // out = (accumulate ? out : 0) + scale * J(x)^T y, J the Jacobian of T at x;
-// with sum != nullptr also sum += scale * J(x)^T y.
+// with sum != nullptr also sum += scale * J(x)^T y.  Four launches, no
+// atomics and no zeroing: the P family, the fused column pass (phase B at x
+// and its transpose), the gathered adjoint of every point, the adjoint of pi.
 template <class T>
 int vjp(agcm_state* s, void* const x[4], const void* const y[4], void* const out[4], double scale, int accumulate,
         cudaStream_t st, void* const* sum = nullptr) {
   const agcm::Geom<T>& G = geom_of<T>(s);
-  const size_t n2 = s->n2, n3 = s->n3, nv = s->nv, e = s->esz;
+  const size_t n2 = s->n2;
   agcm::ColState<T> cs{(T*)s->col[0], (T*)s->col[1], (T*)s->col[2], (T*)s->col[3], (T*)s->col[4], (T*)s->col[5]};
-  // forward phases A and B at x: P family, W, X, psi
   s->prof.begin(KID_COLSTATE, st);
   agcm::k_colstate<T><<<nblocks(n2, 256), 256, 0, st>>>(G, (const T*)x[3], cs);
   s->prof.end(st);
-  s->prof.begin(KID_COLUMN, st);
-  agcm::k_column<T><<<nblocks(n2, 128), 128, 0, st>>>(G, (const T*)x[0], (const T*)x[1], (const T*)x[2],
-                                                      (const T*)x[3], cs, (T*)s->W, (T*)s->X, (T*)s->psi, nullptr,
-                                                      (T*)s->adj2[5], 1.0, nullptr);
+  const agcm::AdjCol<T> c{(T*)s->W, (T*)s->psi, (T*)s->adj3[0], (T*)s->adj3[1], (T*)s->adj2[0], (T*)s->adj2[1]};
+  s->prof.begin(KID_ADJ_COL, st);
+  const dim3 cgrid((unsigned)((G.I + 31) / 32), (unsigned)G.J);
+  // level groups of at most kColL levels, 32 x ng threads (the kernel's bound is 256)
+  const int ng = (G.K + agcm::kColL - 1) / agcm::kColL;
+  if (ng <= 8) {
+    agcm::k_adj_col<T><<<cgrid, dim3(32, ng), 7 * ng * 32 * sizeof(T), st>>>(
+        G, (const T*)x[0], (const T*)x[1], (const T*)x[2], (const T*)x[3], cs, (const T*)y[0], (const T*)y[1],
+        (const T*)y[2], (const T*)y[3], c);
+  } else {
+    agcm::k_adj_col_w<T><<<cgrid, dim3(32, agcm::kColG), 0, st>>>(
+        G, (const T*)x[0], (const T*)x[1], (const T*)x[2], (const T*)x[3], cs, (const T*)y[0], (const T*)y[1],
+        (const T*)y[2], (const T*)y[3], c);
+  }
   s->prof.end(st);
-  agcm::AdjBufs<T> a{};
-  a.aU = (T*)s->adj3[0]; a.aFl = (T*)s->adj3[1]; a.aGu = (T*)s->adj3[2]; a.aGs = (T*)s->adj3[3];
-  a.aPsi = (T*)s->adj3[4]; a.aPhi = (T*)s->adj3[5]; a.tRP = (T*)s->adj3[6]; a.tRPu = (T*)s->adj3[7];
-  a.tPu = (T*)s->adj3[8];
-  a.aV = (T*)s->adjv[0]; a.aFt = (T*)s->adjv[1]; a.aGv = (T*)s->adjv[2]; a.tRPv = (T*)s->adjv[3];
-  a.tPv = (T*)s->adjv[4];
-  a.aW = (T*)s->adjW;
-  a.arPcol = (T*)s->adj2[0]; a.aPiD = (T*)s->adj2[1]; a.mub = (T*)s->adj2[2]; a.mvb = (T*)s->adj2[3];
-  a.mcb = (T*)s->adj2[4];
-  for (int q : {0, 1, 2, 3, 4}) CUDA_TRY(cudaMemsetAsync(s->adj3[q], 0, n3 * e, st));
-  for (int q : {0, 1, 2}) CUDA_TRY(cudaMemsetAsync(s->adjv[q], 0, std::max<size_t>(nv, 1) * e, st));
-  CUDA_TRY(cudaMemsetAsync(s->adjW, 0, (size_t)(G.K + 1) * n2 * e, st));
-  s->prof.begin(KID_ADJ_UPDATE, st);
-  const dim3 agrid((unsigned)((G.I + agcm::kAdjTileX - 1) / agcm::kAdjTileX),
-                   (unsigned)((G.J + agcm::kAdjTileY - 1) / agcm::kAdjTileY));
-  agcm::k_adj_update<T><<<agrid, agcm::kAdjTileX * agcm::kAdjTileY, 0, st>>>(G, (const T*)x[0], (const T*)x[1], (const T*)x[2], cs,
-                                                          (const T*)s->W, (const T*)s->psi, (const T*)y[0],
-                                                          (const T*)y[1], (const T*)y[2], a);
-  s->prof.end(st);
-  s->prof.begin(KID_ADJ_COLUMN, st);
-  agcm::k_adj_column<T><<<nblocks(n2, 128), 128, 0, st>>>(G, (const T*)x[2], cs, (const T*)s->X, (const T*)y[2],
-                                                          (const T*)y[3], a);
+  const agcm::AdjM<T> m{(T*)s->adj2[2], (T*)s->adj2[3], (T*)s->adj2[4]};
+  const agcm::AdjOut<T> o{(T*)out[0], (T*)out[1], (T*)out[2], (T*)out[3],
+                          sum ? (T*)sum[0] : nullptr, sum ? (T*)sum[1] : nullptr,
+                          sum ? (T*)sum[2] : nullptr, sum ? (T*)sum[3] : nullptr, (T)scale, accumulate};
+  s->prof.begin(KID_ADJ_GATHER, st);
+  if (s->n_adj_items > 0) {
+    constexpr size_t smem = agcm::adj_row_smem<T>();
+    static std::atomic<bool> attr{false};
+    if (!attr.load()) {
+      CUDA_TRY(cudaFuncSetAttribute(agcm::k_adj_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      attr.store(true);
+    }
+    agcm::k_adj_rows<T><<<(unsigned)s->n_adj_items, agcm::kAdjRowB, smem, st>>>(
+        G, s->adj_items, (const T*)x[0], (const T*)x[1], (const T*)x[2], cs, (const T*)s->W, (const T*)s->psi,
+        (const T*)s->adj3[0], (const T*)s->adj3[1], (const T*)s->adj2[0], (const T*)y[0], (const T*)y[1],
+        (const T*)y[2], m, o);
+  }
+  if (s->n_adj_rows > 0) {
+    const int nch = (G.K + agcm::kAdjLevChunk - 1) / agcm::kAdjLevChunk;
+    const dim3 agrid((unsigned)((G.I + agcm::kAdjTileX - 1) / agcm::kAdjTileX),
+                     (unsigned)((s->n_adj_rows + agcm::kAdjTileY - 1) / agcm::kAdjTileY), (unsigned)nch);
+    agcm::k_adj_gather<T><<<agrid, agcm::kAdjTileX * agcm::kAdjTileY, 0, st>>>(
+        G, (const T*)x[0], (const T*)x[1], (const T*)x[2], cs, (const T*)s->W, (const T*)s->psi,
+        (const T*)s->adj3[0], (const T*)s->adj3[1], (const T*)s->adj2[0], (const T*)y[0], (const T*)y[1],
+        (const T*)y[2], s->adj_rows, s->n_adj_rows, (T*)s->adj_part, o);
+    agcm::k_adj_fold<T><<<nblocks((size_t)s->n_adj_rows * G.I, 256), 256, 0, st>>>(
+        G, s->adj_rows, s->n_adj_rows, nch, (const T*)s->adj_part, m);
+  }
   s->prof.end(st);
   s->prof.begin(KID_ADJ_COLSTATE, st);
-  agcm::k_adj_conv<T><<<nblocks(n2, 128), 128, 0, st>>>(G, (const T*)x[0], (const T*)x[1], (const T*)x[2], cs, a,
-                                                        (T*)out[0], (T*)out[1], (T*)out[2], (T)scale, accumulate,
-                                                        sum ? (T*)sum[0] : nullptr, sum ? (T*)sum[1] : nullptr,
-                                                        sum ? (T*)sum[2] : nullptr);
-  agcm::k_adj_colstate<T><<<nblocks(n2, 256), 256, 0, st>>>(G, a, (T*)out[3], (T)scale, accumulate,
-                                                            sum ? (T*)sum[3] : nullptr);
+  agcm::k_adj_colstate<T><<<nblocks(n2, 256), 256, 0, st>>>(G, m, (const T*)s->adj2[1], o);
   s->prof.end(st);
   CUDA_TRY(cudaGetLastError());
   return AGCM_OK;

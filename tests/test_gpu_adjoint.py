@@ -34,7 +34,7 @@ def absdot(a, b):
     return sum(float(np.sum(np.abs(a[f] * b[f]))) for f in FIELDS)
 
 
-def setup(I, J, K, seed, kind="random", ones=False):
+def setup(I, J, K, seed, kind="random", ones=False, strides=None):
     if kind == "random":
         st = inputs.random_state(I, J, K, seed=seed)
     elif kind == "rh4":
@@ -44,6 +44,8 @@ def setup(I, J, K, seed, kind="random", ones=False):
     mu = mv = None
     if ones:
         mu, mv = np.ones(J, np.int32), np.ones(J - 1, np.int32)
+    if strides is not None:
+        mu, mv = (np.asarray(a, np.int32) for a in strides)
     g = agcm.Grid(I, J, K, leap_u=mu, leap_v=mv, phis=st["phis"])
     o = oracle.Oracle(I, J, K, leap_u=mu, leap_v=mv, phis=st["phis"])
     x = {f: st[f] for f in FIELDS}
@@ -51,6 +53,7 @@ def setup(I, J, K, seed, kind="random", ones=False):
 
 
 CASES = [(16, 10, 4, "random", False), (20, 9, 3, "random", False), (5, 3, 1, "random", True),
+         (12, 6, 70, "random", False),
          (37, 23, 7, "random", False), (128, 64, 8, "rh4", False), (64, 32, 10, "jet", False)]
 
 
@@ -73,6 +76,29 @@ def test_dot_product_fp64(case):
     after = to_np(s.store())
     for f in FIELDS:
         assert np.array_equal(after[f], x[f])
+
+
+def test_dot_product_fp64_wide_strides():
+    """Rows whose strides reach past the row-segment halo (here 49, 51 and a
+    V-row stride of 53 on 128 longitudes) take the general gather kernel, the
+    other rows (among them the row whose northern V row has stride 53) the
+    row-segment kernel, in one product."""
+    I, J, K = 128, 8, 3
+    mu = [51, 1, 3, 1, 5, 3, 1, 49]
+    mv = [3, 1, 1, 53, 1, 3, 1]
+    g, o, x = setup(I, J, K, 71, strides=(mu, mv))
+    dt = g.dt(100.0) * 0.5
+    for prec, tol in ((agcm.AGCM_FP64, 1e-12), (agcm.AGCM_FP32, 1e-5)):
+        s = agcm.State(g, prec)
+        s.load(x)
+        v = inputs.random_direction(I, J, K, seed=171)
+        lam = inputs.random_direction(I, J, K, seed=271)
+        _, jv = o.step_jvp(x, v, dt, 1)
+        jtl = to_np(s.step_adjoint(lam, dt))
+        lhs, rhs = dot(lam, jv), dot(jtl, v)
+        scale = max(absdot(lam, jv), absdot(jtl, v))
+        assert abs(lhs - rhs) <= tol * scale, (prec, lhs, rhs, scale)
+        s.close()
 
 
 def test_full_transpose_tiny_fp64():
@@ -137,4 +163,38 @@ def test_dot_product_fp64_config3_size():
     lhs, rhs = dot(lam, jv), dot(jtl, v)
     scale = max(absdot(lam, jv), absdot(jtl, v))
     assert abs(lhs - rhs) <= 1e-12 * scale, (lhs, rhs, scale)
+    s.close()
+
+
+@pytest.mark.parametrize("prec", [agcm.AGCM_FP32, agcm.AGCM_FP64], ids=["fp32", "fp64"])
+def test_adjoint_is_deterministic(prec):
+    """Every element of the adjoint is formed by one thread (no atomics), so
+    two calls on the same inputs agree bit for bit; the grid spans many tiles
+    and rows of every stride class."""
+    import torch
+
+    I, J, K = 256, 128, 30
+    g, _, x = setup(I, J, K, 51, "jet")
+    s = agcm.State(g, prec)
+    s.load(x)
+    lam = inputs.random_direction(I, J, K, seed=401)
+    dt = g.dt(100.0)
+    a = s.step_adjoint(lam, dt)
+    b = s.step_adjoint(lam, dt)
+    for f in FIELDS:
+        assert torch.equal(a[f], b[f]), f
+    s.close()
+
+
+def test_adjoint_refuses_aliased_buffers():
+    import ctypes
+
+    I, J, K = 16, 10, 4
+    g, _, x = setup(I, J, K, 61)
+    s = agcm.State(g, agcm.AGCM_FP64)
+    s.load(x)
+    lam = s.empty()
+    ptrs = (ctypes.c_void_p * 4)(*[lam[f].data_ptr() for f in FIELDS])
+    rc = agcm.lib().agcm_step_adjoint(s._h, ptrs, ptrs, 1.0, None)
+    assert rc == agcm.AGCM_EINVAL
     s.close()

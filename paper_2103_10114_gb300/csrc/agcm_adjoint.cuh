@@ -79,7 +79,7 @@ struct AdjCol {
 // the state's precision: FP64 issues at 1/64 of the FP32 rate on this GPU,
 // and per level and column they would be the bulk of the pass.
 //   k_adj_col    groups of at most kColL levels (K <= 8 kColL): walk 1
-//                keeps each level's values in registers for walk 2;
+//                keeps each level's values in shared memory for walk 2;
 //   k_adj_col_w  any K, kColG groups: walk 2 re-forms each level (its loads
 //                hit L1).
 constexpr int kColL = 8;
@@ -194,6 +194,8 @@ struct ColCtx {
   }
 };
 
+__device__ __forceinline__ int gy_off(int gy, int lane) { return gy * 32 + lane; }
+
 // Group sums of one column: sum ds D, sum pb, sum sh aW, sum aW, sum hk B, sum hk_rds xb.
 template <class T>
 struct ColSums {
@@ -239,67 +241,87 @@ __device__ __forceinline__ void col_suffix(const ColCtx<T>& c, const AdjCol<T>& 
   o.Db[q3] = ds * (r.Cb - SW) - c.rPc * (Hkk * xb + ds * SX);
 }
 
+// Four 256-thread blocks per SM (64 registers; the FP64 form keeps two):
+// at 720 x 360 x 30 FP32 0.124 ms against 0.159 ms for two blocks (106
+// registers), the pass being bound by load latency.
+#ifndef AGCM_COLB
+#define AGCM_COLB 4
+#endif
+#ifndef AGCM_COLU
+#define AGCM_COLU 8
+#endif
+constexpr int kColU = AGCM_COLU;
 template <class T>
-__global__ void __launch_bounds__(256) k_adj_col(Geom<T> g, const T* __restrict__ U, const T* __restrict__ V,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? AGCM_COLB : 2) k_adj_col(Geom<T> g, const T* __restrict__ U, const T* __restrict__ V,
                                                  const T* __restrict__ Phi, const T* __restrict__ pi, ColState<T> cs,
                                                  const T* __restrict__ yU, const T* __restrict__ yV,
                                                  const T* __restrict__ yPhi, const T* __restrict__ ypi,
                                                  AdjCol<T> o) {
   extern __shared__ __align__(16) unsigned char col_smem[];
-  T* const red = reinterpret_cast<T*>(col_smem);
+  T* const red = reinterpret_cast<T*>(col_smem);  // [7][G][32]: group sums, then arp
   const int I = g.I, K = g.K, G = blockDim.y;
+  // each level's D, psi adjoint, Phi, ybar_Phi and W adjoint: [5][kColL][G][32]
+  T* const lv = red + 7 * G * 32 + gy_off(threadIdx.y, threadIdx.x);
+  const int lstride = G * 32;
   const int lane = threadIdx.x, gy = threadIdx.y;
   const int i = blockIdx.x * 32 + lane, j = blockIdx.y;
   const bool col = i < I;
   const ColCtx<T> c(g, U, V, Phi, cs, yU, yV, yPhi, col ? i : 0, j);
   const int kb = min(K, gy * kColL), ke = min(K, kb + kColL);
   const size_t n = c.r2 + c.ic;
-  // ---- walk 1: every level's values into registers, and the group sums
-  T vD[kColL], vP[kColL], vPh[kColL], vY[kColL], vA[kColL];
+  // ---- walk 1: every level's values into shared memory, and the group sums
+  auto vD = [&](int l) -> T& { return lv[(0 * kColL + l) * lstride]; };
+  auto vP = [&](int l) -> T& { return lv[(1 * kColL + l) * lstride]; };
+  auto vPh = [&](int l) -> T& { return lv[(2 * kColL + l) * lstride]; };
+  auto vY = [&](int l) -> T& { return lv[(3 * kColL + l) * lstride]; };
+  auto vA = [&](int l) -> T& { return lv[(4 * kColL + l) * lstride]; };
   T s[6] = {0, 0, 0, 0, 0, 0};
   typename ColCtx<T>::Lev cv{}, pv{};
   if (kb > 0 && kb < ke) c.level(kb - 1, pv);
-#pragma unroll
+#pragma unroll kColU
   for (int l = 0; l < kColL; ++l) {
     const int k = kb + l;
     if (k < ke) {
       c.level(k, cv);
-      vD[l] = cv.D;
-      vP[l] = cv.pb;
-      vPh[l] = cv.ph;
-      vY[l] = cv.yx;
-      vA[l] = k > 0 ? c.adj_w(k, cv, pv) : T(0);
+      const T aw = k > 0 ? c.adj_w(k, cv, pv) : T(0);
+      vD(l) = cv.D;
+      vP(l) = cv.pb;
+      vPh(l) = cv.ph;
+      vY(l) = cv.yx;
+      vA(l) = aw;
       s[0] += ldg(g.ds + k) * cv.D;
       s[1] += cv.pb;
-      s[2] += (T(1) - ldg(g.oms + k)) * vA[l];  // sh_k aW_k (vA = 0 at k = 0)
-      s[3] += vA[l];
+      s[2] += (T(1) - ldg(g.oms + k)) * aw;  // sh_k aW_k (aW = 0 at k = 0)
+      s[3] += aw;
       s[4] += ldg(g.hk + k) * c.Bk(k, cv.ph);
       s[5] += ldg(g.hk_rds + k) * c.xbk(k, cv.ph, cv.yx);
       pv = cv;
     }
   }
   ColSums<T> r = col_exchange(red, G, gy, lane, s);
-  // ---- walk 2: the outputs of every level, from registers
+  // ---- walk 2: the outputs of every level, from shared memory (each thread
+  // reads back only what it wrote)
   T arp = 0;
   if (col && kb < ke) {
     r.Cb -= ldg(ypi + n);
     const T ps = ldg(g.rt0pit + n) * ldg(pi + n);
     T qD = 0, qB = 0, qX = 0, qA = 0, Q = r.Q, pre = r.pre;
-#pragma unroll
+#pragma unroll kColU
     for (int l = 0; l < kColL; ++l) {
       const int k = kb + l;
       if (k < ke) {
         const size_t q3 = (size_t)k * c.plane + n;
-        o.aPhi[q3] = c.adj_phi(k, vD[l], vP[l], vPh[l], vY[l], Q, pre, arp);
-        Q += ldg(g.ds + k) * vD[l];
-        pre += vP[l];
-        const T B = c.Bk(k, vPh[l]), xb = c.xbk(k, vPh[l], vY[l]);
+        const T D = vD(l), pb = vP(l), ph = vPh(l), yx = vY(l);
+        o.aPhi[q3] = c.adj_phi(k, D, pb, ph, yx, Q, pre, arp);
+        Q += ldg(g.ds + k) * D;
+        pre += pb;
+        const T B = c.Bk(k, ph), xb = c.xbk(k, ph, yx);
         const T qD0 = qD;
-        qD += ldg(g.ds + k) * vD[l];
+        qD += ldg(g.ds + k) * D;
         qB += ldg(g.hk + k) * B;
         qX += ldg(g.hk_rds + k) * xb;
-        qA += vA[l];
-        col_suffix(c, o, k, q3, vD[l], B, xb, qD0, qB, qX, qA, s[0], s[4], s[5], s[3], r, ps);
+        qA += vA(l);
+        col_suffix(c, o, k, q3, D, B, xb, qD0, qB, qX, qA, s[0], s[4], s[5], s[3], r, ps);
       }
     }
   }
@@ -706,7 +728,10 @@ constexpr size_t adj_row_smem() {
 }
 
 template <class T>
-__global__ void __launch_bounds__(kAdjRowB, 2) k_adj_rows(
+#ifndef AGCM_ADJROWB
+#define AGCM_ADJROWB 2
+#endif
+__global__ void __launch_bounds__(kAdjRowB, sizeof(T) == 4 ? AGCM_ADJROWB : 1) k_adj_rows(
     Geom<T> g, const int* __restrict__ items, const T* __restrict__ U, const T* __restrict__ V,
     const T* __restrict__ Phi, ColState<T> cs, const T* __restrict__ W, const T* __restrict__ psi,
     const T* __restrict__ Db, const T* __restrict__ aPhi, const T* __restrict__ arPcol, const T* __restrict__ yU,
@@ -801,6 +826,11 @@ __global__ void __launch_bounds__(kAdjRowB, 2) k_adj_rows(
   Own ocur{}, onxt{};
   if (active) load_raw(0, cur);
   if (owner) load_own(0, ocur);
+  // the array the owner reads back and adds to: the stage sum, or the
+  // output itself when accumulating
+  T* const rmwU = o.sU ? o.sU : (o.accumulate ? o.oU : nullptr);
+  T* const rmwP = o.sU ? o.sPhi : (o.accumulate ? o.oPhi : nullptr);
+  T* const rmwV = o.sU ? o.sV : (o.accumulate ? o.oV : nullptr);
   // own column at level k-1 (row j, V row j)
   T yPp = 0, Pp = 0, yUp = 0, Up = 0, yVp = 0, Vp = 0;
   // W at level k (rows j, j+1; columns i, i+1), loaded one level ahead
@@ -809,6 +839,15 @@ __global__ void __launch_bounds__(kAdjRowB, 2) k_adj_rows(
   const T rPc = rP0, rPuc = rPu0, Puc = Pu0, rPvc = rPv0, Pvc = Pv0;
   for (int k = 0; k < K; ++k) {
     T* const b = sm + (size_t)(k & 1) * kAdjRowNA * kAdjRowB;
+    // this level's values to add to, loaded before the staging so that the
+    // load is in flight across it
+    T accU = 0, accP = 0, accV = 0;
+    if (owner && rmwU) {
+      const size_t q = (size_t)k * plane + r2 + c;
+      accU = rmwU[q];
+      accP = rmwP[q];
+      if (hasS) accV = rmwV[(size_t)k * vplane + r2 + c];
+    }
     if (active) {
       T* const q = b + t;
       const Raw& r = cur;
@@ -893,8 +932,12 @@ __global__ void __launch_bounds__(kAdjRowB, 2) k_adj_rows(
       {
         const size_t q = r3 + c;
         const T v = o.scale * bu;
-        o.oU[q] = (o.accumulate ? o.oU[q] : T(0)) + v;
-        if (o.sU) o.sU[q] += v;
+        if (o.sU) {
+          o.oU[q] = v;
+          o.sU[q] = accU + v;
+        } else {
+          o.oU[q] = accU + v;  // accU = 0 unless accumulating
+        }
       }
       // ---------------- Phi point
       T aGs = -r2A * zf * (A(kqP0, -M) * Fla1 - A(kqP0, M) * Flb1);
@@ -910,8 +953,12 @@ __global__ void __launch_bounds__(kAdjRowB, 2) k_adj_rows(
       {
         const size_t q = r3 + c;
         const T v = o.scale * bp;
-        o.oPhi[q] = (o.accumulate ? o.oPhi[q] : T(0)) + v;
-        if (o.sU) o.sPhi[q] += v;
+        if (o.sU) {
+          o.oPhi[q] = v;
+          o.sPhi[q] = accP + v;
+        } else {
+          o.oPhi[q] = accP + v;
+        }
       }
       // ---------------- V point
       if (hasS) {
@@ -944,8 +991,12 @@ __global__ void __launch_bounds__(kAdjRowB, 2) k_adj_rows(
         arPv += aGv * Vc + tRPv;
         const size_t q = rv + c;
         const T v = o.scale * bv;
-        o.oV[q] = (o.accumulate ? o.oV[q] : T(0)) + v;
-        if (o.sU) o.sV[q] += v;
+        if (o.sU) {
+          o.oV[q] = v;
+          o.sV[q] = accV + v;
+        } else {
+          o.oV[q] = accV + v;
+        }
       }
       yPp = yPc; Pp = Pc; yUp = yUc; Up = Uc; yVp = yVc; Vp = Vc;
       Wt = Wb; Wtp = Wbp; Wts = Wbs;

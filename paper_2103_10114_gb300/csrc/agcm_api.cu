@@ -1276,7 +1276,7 @@ int vjp(agcm_state* s, void* const x[4], const void* const y[4], void* const out
   // level groups of at most kColL levels, 32 x ng threads (the kernel's bound is 256)
   const int ng = (G.K + agcm::kColL - 1) / agcm::kColL;
   if (ng <= 8) {
-    agcm::k_adj_col<T><<<cgrid, dim3(32, ng), 7 * ng * 32 * sizeof(T), st>>>(
+    agcm::k_adj_col<T><<<cgrid, dim3(32, ng), (7 + 5 * agcm::kColL) * ng * 32 * sizeof(T), st>>>(
         G, (const T*)x[0], (const T*)x[1], (const T*)x[2], (const T*)x[3], cs, (const T*)y[0], (const T*)y[1],
         (const T*)y[2], (const T*)y[3], c);
   } else {
@@ -1290,6 +1290,25 @@ int vjp(agcm_state* s, void* const x[4], const void* const y[4], void* const out
                           sum ? (T*)sum[0] : nullptr, sum ? (T*)sum[1] : nullptr,
                           sum ? (T*)sum[2] : nullptr, sum ? (T*)sum[3] : nullptr, (T)scale, accumulate};
   s->prof.begin(KID_ADJ_GATHER, st);
+  // the rows of the L1 form run on the state's second stream beside the
+  // row-segment kernel (they write other rows)
+  const bool fork = s->n_adj_items > 0 && s->n_adj_rows > 0 && s->aux;
+  if (fork) {
+    CUDA_TRY(cudaEventRecord(s->ev_fork, st));
+    CUDA_TRY(cudaStreamWaitEvent(s->aux, s->ev_fork, 0));
+  }
+  if (s->n_adj_rows > 0) {
+    cudaStream_t q = fork ? s->aux : st;
+    const int nch = (G.K + agcm::kAdjLevChunk - 1) / agcm::kAdjLevChunk;
+    const dim3 agrid((unsigned)((G.I + agcm::kAdjTileX - 1) / agcm::kAdjTileX),
+                     (unsigned)((s->n_adj_rows + agcm::kAdjTileY - 1) / agcm::kAdjTileY), (unsigned)nch);
+    agcm::k_adj_gather<T><<<agrid, agcm::kAdjTileX * agcm::kAdjTileY, 0, q>>>(
+        G, (const T*)x[0], (const T*)x[1], (const T*)x[2], cs, (const T*)s->W, (const T*)s->psi,
+        (const T*)s->adj3[0], (const T*)s->adj3[1], (const T*)s->adj2[0], (const T*)y[0], (const T*)y[1],
+        (const T*)y[2], s->adj_rows, s->n_adj_rows, (T*)s->adj_part, o);
+    agcm::k_adj_fold<T><<<nblocks((size_t)s->n_adj_rows * G.I, 256), 256, 0, q>>>(
+        G, s->adj_rows, s->n_adj_rows, nch, (const T*)s->adj_part, m);
+  }
   if (s->n_adj_items > 0) {
     constexpr size_t smem = agcm::adj_row_smem<T>();
     static std::atomic<bool> attr{false};
@@ -1302,16 +1321,9 @@ int vjp(agcm_state* s, void* const x[4], const void* const y[4], void* const out
         (const T*)s->adj3[0], (const T*)s->adj3[1], (const T*)s->adj2[0], (const T*)y[0], (const T*)y[1],
         (const T*)y[2], m, o);
   }
-  if (s->n_adj_rows > 0) {
-    const int nch = (G.K + agcm::kAdjLevChunk - 1) / agcm::kAdjLevChunk;
-    const dim3 agrid((unsigned)((G.I + agcm::kAdjTileX - 1) / agcm::kAdjTileX),
-                     (unsigned)((s->n_adj_rows + agcm::kAdjTileY - 1) / agcm::kAdjTileY), (unsigned)nch);
-    agcm::k_adj_gather<T><<<agrid, agcm::kAdjTileX * agcm::kAdjTileY, 0, st>>>(
-        G, (const T*)x[0], (const T*)x[1], (const T*)x[2], cs, (const T*)s->W, (const T*)s->psi,
-        (const T*)s->adj3[0], (const T*)s->adj3[1], (const T*)s->adj2[0], (const T*)y[0], (const T*)y[1],
-        (const T*)y[2], s->adj_rows, s->n_adj_rows, (T*)s->adj_part, o);
-    agcm::k_adj_fold<T><<<nblocks((size_t)s->n_adj_rows * G.I, 256), 256, 0, st>>>(
-        G, s->adj_rows, s->n_adj_rows, nch, (const T*)s->adj_part, m);
+  if (fork) {
+    CUDA_TRY(cudaEventRecord(s->ev_join, s->aux));
+    CUDA_TRY(cudaStreamWaitEvent(st, s->ev_join, 0));
   }
   s->prof.end(st);
   s->prof.begin(KID_ADJ_COLSTATE, st);

@@ -56,15 +56,25 @@ NCU_OPS = {
 }
 
 
-def kernel_source_hash():
-    """sha1 of the stage kernels' sources (the row-segment and column kernels)."""
+# DRAM traffic of one FP32 adjoint step at 720x360x30 (all its launches: the
+# forward recompute of the two stage states and three adjoint products), from
+# an ncu capture, valid while the kernel sources are the captured ones.
+NCU_ADJ = ("401583f13b6616b2d1545b50f4972059004af20f", 2830007552)
+
+
+def kernel_source_hash(names=("agcm_row.cuh", "agcm_fused.cuh", "agcm_common.cuh")):
+    """sha1 of kernel sources (by default the stage kernels: the row-segment
+    and column kernels)."""
     import hashlib
 
     h = hashlib.sha1()
-    for name in ("agcm_row.cuh", "agcm_fused.cuh", "agcm_common.cuh"):
+    for name in names:
         with open(os.path.join(ROOT, "paper_2103_10114_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
+
+
+ADJ_SOURCES = ("agcm_adjoint.cuh", "agcm_phases.cuh", "agcm_row.cuh", "agcm_fused.cuh", "agcm_common.cuh")
 
 
 def peaks():
@@ -740,6 +750,11 @@ def measure_adjoint(agcm, inputs, torch, steps=5):
         lam = s.store()
         s.step_adjoint(lam, dt)
         ms = _time(torch, lambda: s.step_adjoint(lam, dt), steps)
+        s.profile(True)
+        s.step_adjoint(lam, dt)
+        torch.cuda.synchronize()
+        kern = {k: round(v[0], 4) for k, v in s.profile_read().items()}
+        s.profile(False)
         s.step(1, dt)
         fms = _time(torch, lambda: s.step(1, dt), steps)
         # bytes model of one adjoint step: the forward recompute (24 words)
@@ -748,7 +763,11 @@ def measure_adjoint(agcm, inputs, torch, steps=5):
         rate = I * J * K / (ms / 1e3)
         res[tag] = {"value": rate, "unit": "gp-steps/s", "ms_per_adjoint_step": ms,
                     "ms_per_forward_step": fms, "adjoint_over_forward": ms / fms,
-                    "bytes_per_point_step": 54 * esz, "hbm_frac_step": rate * 54 * esz / (peaks()[0] * 1e9)}
+                    "bytes_per_point_step": 54 * esz, "hbm_frac_step": rate * 54 * esz / (peaks()[0] * 1e9),
+                    "kernel_ms_per_step": kern}
+        if prec == agcm.AGCM_FP32 and NCU_ADJ[0] and NCU_ADJ[0] == kernel_source_hash(ADJ_SOURCES):
+            res[tag]["ncu_dram_bytes_per_step"] = NCU_ADJ[1]
+            res[tag]["ncu_traffic_over_model"] = NCU_ADJ[1] / (54 * esz * I * J * K)
         s.close()
     return res
 

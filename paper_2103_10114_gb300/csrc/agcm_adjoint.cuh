@@ -82,25 +82,55 @@ struct AdjCol {
 //                keeps each level's values in shared memory for walk 2;
 //   k_adj_col_w  any K, kColG groups: walk 2 re-forms each level (its loads
 //                hit L1).
-constexpr int kColL = 8;
+#ifndef AGCM_COLL
+#define AGCM_COLL 8
+#endif
+constexpr int kColL = AGCM_COLL;
 #ifndef AGCM_COLG
 #define AGCM_COLG 2
 #endif
 constexpr int kColG = AGCM_COLG;
 
-// The per-column pieces shared by the two forms.
+// The per-column pieces shared by the two forms.  ST: the level tables are
+// read from a copy in shared memory (8 values per level: ds, Hkk, hk, hk_rds,
+// r2ds, 1 - sh, rho), else from the grid's tables in global memory.
+enum { kLds, kLHkk, kLhk, kLhkr, kLr2ds, kLoms, kLrho, kLN = 8 };
 template <class T>
+__device__ __forceinline__ void col_tables(const Geom<T>& g, T* lt, int tid, int nthreads) {
+  for (int k = tid; k < g.K; k += nthreads) {
+    T* L = lt + kLN * k;
+    L[kLds] = g.ds[k];
+    L[kLHkk] = g.Hkk[k];
+    L[kLhk] = g.hk[k];
+    L[kLhkr] = g.hk_rds[k];
+    L[kLr2ds] = g.r2ds[k];
+    L[kLoms] = g.oms[k];
+    L[kLrho] = g.nl ? g.rho[k] : T(0);
+    L[7] = T(0);
+  }
+}
+template <class T, bool ST>
 struct ColCtx {
   const Geom<T>& g;
+  const T* lt = nullptr;  // shared-memory level tables (ST)
   const T *U, *V, *Phi, *yU, *yV, *yPhi;
   size_t plane, vplane, r2;
   int ic, ue, uw, im;
   bool hasS, hasN, nl;
   T rdx, rdy, rady, svS, svN, Pue, Puw, rPc, rPui, rPum, PvS, PvN, rPvS, rPvN;
 
-  __device__ ColCtx(const Geom<T>& g_, const T* U_, const T* V_, const T* Phi_, const ColState<T>& cs,
-                    const T* yU_, const T* yV_, const T* yPhi_, int i, int j)
-      : g(g_), U(U_), V(V_), Phi(Phi_), yU(yU_), yV(yV_), yPhi(yPhi_) {
+  __device__ T tab(int k, int f) const {
+    if constexpr (ST) {
+      return lt[kLN * k + f];
+    } else {
+      const T* p = f == kLds ? g.ds : f == kLHkk ? g.Hkk : f == kLhk ? g.hk : f == kLhkr ? g.hk_rds
+                 : f == kLr2ds ? g.r2ds : f == kLoms ? g.oms : g.rho;
+      return ldg(p + k);
+    }
+  }
+  __device__ ColCtx(const Geom<T>& g_, const T* lt_, const T* U_, const T* V_, const T* Phi_,
+                    const ColState<T>& cs, const T* yU_, const T* yV_, const T* yPhi_, int i, int j)
+      : g(g_), lt(lt_), U(U_), V(V_), Phi(Phi_), yU(yU_), yV(yV_), yPhi(yPhi_) {
     const int I = g.I, J = g.J;
     plane = (size_t)J * I;
     vplane = (size_t)(J - 1) * I;
@@ -163,7 +193,7 @@ struct ColCtx {
   // adjoint of W_k: vb(k-1) G(k) - vb(k) G(k-1) at the five points,
   // vb = -y r2ds / P (the U and V points hold W(j, i) in a face mean, weight 1/2)
   __device__ T adj_w(int k, const Lev& c, const Lev& p) const {
-    const T r = ldg(g.r2ds + k), rm = ldg(g.r2ds + k - 1);
+    const T r = tab(k, kLr2ds), rm = tab(k - 1, kLr2ds);
     const T aw = r * c.q[0] * p.x[0] - rm * p.q[0] * c.x[0];
     T h = 0;
 #pragma unroll
@@ -172,22 +202,22 @@ struct ColCtx {
   }
   __device__ T Bk(int k, T ph) const {
     T B = rPc * ph;
-    if (nl) B *= T(1) + ldg(g.rho + k) * B;
+    if (nl) B *= T(1) + tab(k, kLrho) * B;
     return B;
   }
   // Omega~ carries c_k: its D-dependence is that of -c_k S_k / P
-  __device__ T xbk(int k, T ph, T yx) const { return nl ? yx * (T(1) + ldg(g.rho + k) * rPc * ph) : yx; }
+  __device__ T xbk(int k, T ph, T yx) const { return nl ? yx * (T(1) + tab(k, kLrho) * rPc * ph) : yx; }
   // the prefix quantities of level k: the adjoint of Phi, and arp += the
   // adjoint of 1/P (Q, pre: the prefix sums before level k)
   __device__ T adj_phi(int k, T D, T pb, T ph, T yx, T Q, T pre, T& arp) const {
-    const T Hkk = ldg(g.Hkk + k);
-    const T Sk = Hkk * D + ldg(g.hk_rds + k) * Q;
-    const T Bb = Hkk * pb + ldg(g.hk + k) * pre;
+    const T Hkk = tab(k, kLHkk);
+    const T Sk = Hkk * D + tab(k, kLhkr) * Q;
+    const T Bb = Hkk * pb + tab(k, kLhk) * pre;
     if (!nl) {
       arp += Bb * ph - yx * Sk;
       return Bb * rPc;
     }
-    const T rho = ldg(g.rho + k), G = rPc * ph;
+    const T rho = tab(k, kLrho), G = rPc * ph;
     const T Gb = Bb * (T(1) + T(2) * rho * G) - yx * rPc * rho * Sk;  // dB/dG = 1 + 2 rho G
     arp += Gb * ph - yx * (T(1) + rho * G) * Sk;
     return Gb * rPc;
@@ -229,13 +259,12 @@ __device__ __forceinline__ ColSums<T> col_exchange(T* red, int G, int gy, int la
 // The suffix quantities of level k: W_k, psi_k, Dbar_k.  q*: this group's
 // sums up to level k (qD before it, the others including it), s*: this
 // group's totals, r: the other groups' offsets.
-template <class T>
-__device__ __forceinline__ void col_suffix(const ColCtx<T>& c, const AdjCol<T>& o, int k, size_t q3, T D, T B,
+template <class T, bool ST>
+__device__ __forceinline__ void col_suffix(const ColCtx<T, ST>& c, const AdjCol<T>& o, int k, size_t q3, T D, T B,
                                            T xb, T qD, T qB, T qX, T qA, T sD, T sB, T sX, T sA,
                                            const ColSums<T>& r, T ps) {
-  const Geom<T>& g = c.g;
-  const T ds = ldg(g.ds + k), Hkk = ldg(g.Hkk + k);
-  if (k > 0) o.W[q3] = r.Rs + (sD - qD) - ldg(g.oms + k) * r.C;  // sum_{k' >= k} ds D - (1 - sh_k) C
+  const T ds = c.tab(k, kLds), Hkk = c.tab(k, kLHkk);
+  if (k > 0) o.W[q3] = r.Rs + (sD - qD) - c.tab(k, kLoms) * r.C;  // sum_{k' >= k} ds D - (1 - sh_k) C
   o.psi[q3] = Hkk * B + (r.Ss + (sB - qB)) + ps;
   const T SW = r.SWs + (sA - qA), SX = r.SXs + (sX - qX);
   o.Db[q3] = ds * (r.Cb - SW) - c.rPc * (Hkk * xb + ds * SX);
@@ -260,13 +289,17 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? AGCM_COLB : 2) k_adj_col
   extern __shared__ __align__(16) unsigned char col_smem[];
   T* const red = reinterpret_cast<T*>(col_smem);  // [7][G][32]: group sums, then arp
   const int I = g.I, K = g.K, G = blockDim.y;
-  // each level's D, psi adjoint, Phi, ybar_Phi and W adjoint: [5][kColL][G][32]
+  // each level's D, psi adjoint, Phi, ybar_Phi and W adjoint: [5][kColL][G][32];
+  // then the level tables [K][8]
   T* const lv = red + 7 * G * 32 + gy_off(threadIdx.y, threadIdx.x);
+  T* const lt = red + (7 + 5 * kColL) * G * 32;
   const int lstride = G * 32;
   const int lane = threadIdx.x, gy = threadIdx.y;
   const int i = blockIdx.x * 32 + lane, j = blockIdx.y;
   const bool col = i < I;
-  const ColCtx<T> c(g, U, V, Phi, cs, yU, yV, yPhi, col ? i : 0, j);
+  col_tables(g, lt, gy * 32 + lane, G * 32);
+  __syncthreads();
+  const ColCtx<T, true> c(g, lt, U, V, Phi, cs, yU, yV, yPhi, col ? i : 0, j);
   const int kb = min(K, gy * kColL), ke = min(K, kb + kColL);
   const size_t n = c.r2 + c.ic;
   // ---- walk 1: every level's values into shared memory, and the group sums
@@ -276,7 +309,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? AGCM_COLB : 2) k_adj_col
   auto vY = [&](int l) -> T& { return lv[(3 * kColL + l) * lstride]; };
   auto vA = [&](int l) -> T& { return lv[(4 * kColL + l) * lstride]; };
   T s[6] = {0, 0, 0, 0, 0, 0};
-  typename ColCtx<T>::Lev cv{}, pv{};
+  typename ColCtx<T, true>::Lev cv{}, pv{};
   if (kb > 0 && kb < ke) c.level(kb - 1, pv);
 #pragma unroll kColU
   for (int l = 0; l < kColL; ++l) {
@@ -289,12 +322,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? AGCM_COLB : 2) k_adj_col
       vPh(l) = cv.ph;
       vY(l) = cv.yx;
       vA(l) = aw;
-      s[0] += ldg(g.ds + k) * cv.D;
+      s[0] += c.tab(k, kLds) * cv.D;
       s[1] += cv.pb;
-      s[2] += (T(1) - ldg(g.oms + k)) * aw;  // sh_k aW_k (aW = 0 at k = 0)
+      s[2] += (T(1) - c.tab(k, kLoms)) * aw;  // sh_k aW_k (aW = 0 at k = 0)
       s[3] += aw;
-      s[4] += ldg(g.hk + k) * c.Bk(k, cv.ph);
-      s[5] += ldg(g.hk_rds + k) * c.xbk(k, cv.ph, cv.yx);
+      s[4] += c.tab(k, kLhk) * c.Bk(k, cv.ph);
+      s[5] += c.tab(k, kLhkr) * c.xbk(k, cv.ph, cv.yx);
       pv = cv;
     }
   }
@@ -313,13 +346,14 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? AGCM_COLB : 2) k_adj_col
         const size_t q3 = (size_t)k * c.plane + n;
         const T D = vD(l), pb = vP(l), ph = vPh(l), yx = vY(l);
         o.aPhi[q3] = c.adj_phi(k, D, pb, ph, yx, Q, pre, arp);
-        Q += ldg(g.ds + k) * D;
+        const T dsk = c.tab(k, kLds);
+        Q += dsk * D;
         pre += pb;
         const T B = c.Bk(k, ph), xb = c.xbk(k, ph, yx);
         const T qD0 = qD;
-        qD += ldg(g.ds + k) * D;
-        qB += ldg(g.hk + k) * B;
-        qX += ldg(g.hk_rds + k) * xb;
+        qD += dsk * D;
+        qB += c.tab(k, kLhk) * B;
+        qX += c.tab(k, kLhkr) * xb;
         qA += vA(l);
         col_suffix(c, o, k, q3, D, B, xb, qD0, qB, qX, qA, s[0], s[4], s[5], s[3], r, ps);
       }
@@ -348,12 +382,12 @@ __global__ void __launch_bounds__(32 * kColG) k_adj_col_w(Geom<T> g, const T* __
   const int lane = threadIdx.x, gy = threadIdx.y;
   const int i = blockIdx.x * 32 + lane, j = blockIdx.y;
   const bool col = i < I;
-  const ColCtx<T> c(g, U, V, Phi, cs, yU, yV, yPhi, col ? i : 0, j);
+  const ColCtx<T, false> c(g, nullptr, U, V, Phi, cs, yU, yV, yPhi, col ? i : 0, j);
   const int L = (K + kColG - 1) / kColG;
   const int kb = min(K, gy * L), ke = min(K, kb + L);
   const size_t n = c.r2 + c.ic;
   T s[6] = {0, 0, 0, 0, 0, 0};
-  typename ColCtx<T>::Lev cv{}, pv{};
+  typename ColCtx<T, false>::Lev cv{}, pv{};
   if (kb < ke) {
     if (kb > 0) c.level(kb - 1, pv);
     for (int k = kb; k < ke; ++k) {

@@ -1276,7 +1276,13 @@ int vjp(agcm_state* s, void* const x[4], const void* const y[4], void* const out
   // level groups of at most kColL levels, 32 x ng threads (the kernel's bound is 256)
   const int ng = (G.K + agcm::kColL - 1) / agcm::kColL;
   if (ng <= 8) {
-    agcm::k_adj_col<T><<<cgrid, dim3(32, ng), (7 + 5 * agcm::kColL) * ng * 32 * sizeof(T), st>>>(
+    const size_t smem = ((7 + 5 * agcm::kColL) * ng * 32 + agcm::kLN * G.K) * sizeof(T);
+    static std::atomic<size_t> attr{0};  // the size set so far
+    if (attr.load() < smem) {
+      CUDA_TRY(cudaFuncSetAttribute(agcm::k_adj_col<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      attr.store(smem);
+    }
+    agcm::k_adj_col<T><<<cgrid, dim3(32, ng), smem, st>>>(
         G, (const T*)x[0], (const T*)x[1], (const T*)x[2], (const T*)x[3], cs, (const T*)y[0], (const T*)y[1],
         (const T*)y[2], (const T*)y[3], c);
   } else {

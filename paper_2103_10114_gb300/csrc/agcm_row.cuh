@@ -36,6 +36,8 @@
 // or two rows nearest each pole at 0.25 deg) and grids whose rows are not
 // 16-byte aligned run the global-load kernel instead.
 #pragma once
+#include <type_traits>
+
 #include "agcm_common.cuh"
 
 namespace agcm {
@@ -50,12 +52,11 @@ constexpr int kRowDesc = 48;       // copy descriptors per CTA: 12 rows of at mo
 #ifndef AGCM_ROW_MINB
 #define AGCM_ROW_MINB (768 / AGCM_ROW_B)  // resident CTAs per SM: 24 warps at <= 80 registers
 #endif
-#ifndef AGCM_ROW_R
-#define AGCM_ROW_R 2
-#endif
+// levels in flight: a ring of two slots (three measured slower), which the
+// level loop pairs with the two published buffers
 template <class T>
 struct RowCfg {
-  static constexpr int R = sizeof(T) == 4 ? AGCM_ROW_R : 2;  // levels in flight
+  static constexpr int R = 2;
 };
 
 // Halo of row j: one more than the largest stride of its stencil, to a
@@ -460,10 +461,14 @@ __device__ __forceinline__ void row_segment(const Geom<T>& g, const RowArgs<T>& 
     }
   };
 
-  int slot = 0;
-  unsigned ph = 0;   // ring slot of the level and the parity of its current use
-  int buf = 0;       // published buffer of the level
-  for (int k = K - 1; k >= 0; --k) {
+  // The level loop runs in pairs: with two ring slots, the level of
+  // iteration q uses slot q % 2 and published buffer q % 2, so each half of a
+  // pair has its slot and buffer fixed at compile time and the carries pass
+  // from one half to the other without copies.
+  static_assert(R == 2, "the level loop pairs the two ring slots");
+  unsigned ph = 0;  // parity of the current use of both slots
+  auto level = [&](const int k, auto SL) {
+    constexpr int slot = decltype(SL)::value, buf = slot;
     mbar_wait_bounded(bar + slot, ph, abort_flag, a.err);
     const T* rw = ring + (size_t)slot * kRowRaw * NTP;
     const T* raw = rw + t;
@@ -584,12 +589,14 @@ __device__ __forceinline__ void row_segment(const Geom<T>& g, const RowArgs<T>& 
     pbU = nbU;
     pbV = nbV;
     pbPh = nbPh;
-    if (++slot == R) {
-      slot = 0;
-      ph ^= 1u;
-    }
-    buf ^= 1;
+  };
+  int k = K - 1;
+  for (; k >= 1; k -= 2) {
+    level(k, std::integral_constant<int, 0>{});
+    level(k - 1, std::integral_constant<int, 1>{});
+    ph ^= 1u;
   }
+  if (k == 0) level(0, std::integral_constant<int, 0>{});
   // level 0 has no level above: its top-face flux W_0 G_{-1} is zero
   complete(0, T(0), T(0), T(0));
   if (owned && a.Ubar_o) {

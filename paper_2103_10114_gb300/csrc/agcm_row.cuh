@@ -307,15 +307,21 @@ __device__ __forceinline__ void row_segment(const Geom<T>& g, const RowArgs<T>& 
   const int warp = __shfl_sync(0xffffffffu, t >> 5, 0);
   const int ndesc = *s_ndesc;
   const unsigned txb = *s_tx;
-  // a warp's first two descriptors are read once, for every level
+  // a warp's first two descriptors are read once, for every level; the
+  // levels are issued from the surface up, one after the other, so their
+  // sources step down one plane per level from one past the surface level
   RowDesc d0{nullptr, 0, 0, 0}, d1{nullptr, 0, 0, 0};
   if (warp < ndesc) d0 = desc[warp];
   if (warp + nw < ndesc) d1 = desc[warp + nw];
+  const char* src0 = d0.src0 + (unsigned long long)K * d0.plane_bytes;
+  const char* src1 = d1.src0 + (unsigned long long)K * d1.plane_bytes;
   auto issue_level = [&](int kk, int s) {
     if (warp == 0) mbar_expect_tx_warp(bar + s, txb);
     const unsigned base = ring_s + (unsigned)(s * kRowRaw * NTP * sizeof(T));
-    if (d0.bytes) bulk_copy_g2s_warp(base + d0.dst, d0.src0 + (unsigned long long)kk * d0.plane_bytes, d0.bytes, bar + s);
-    if (d1.bytes) bulk_copy_g2s_warp(base + d1.dst, d1.src0 + (unsigned long long)kk * d1.plane_bytes, d1.bytes, bar + s);
+    src0 -= d0.plane_bytes;
+    src1 -= d1.plane_bytes;
+    if (d0.bytes) bulk_copy_g2s_warp(base + d0.dst, src0, d0.bytes, bar + s);
+    if (d1.bytes) bulk_copy_g2s_warp(base + d1.dst, src1, d1.bytes, bar + s);
     for (int d = warp + 2 * nw; d < ndesc; d += nw) {  // segments of fewer than six warps
       const RowDesc e = desc[d];
       bulk_copy_g2s_warp(base + e.dst, e.src0 + (unsigned long long)kk * e.plane_bytes, e.bytes, bar + s);
@@ -432,18 +438,24 @@ __device__ __forceinline__ void row_segment(const Geom<T>& g, const RowArgs<T>& 
   // element offsets fit 32 bits: nlon * nlat * nlev <= 4e9
   const unsigned plane = (unsigned)J * (unsigned)I, vplane = (unsigned)(J - 1) * (unsigned)I;
   const unsigned o_own = (unsigned)j * (unsigned)I + (unsigned)gc;
+  // outputs of the own column, stepped down one plane per completed level
+  // (the levels complete from the surface up, one after the other)
+  T* oPhp = a.Phio + (size_t)K * plane + o_own;
+  T* oUp = a.Uo + (size_t)K * plane + o_own;
+  T* oVp = hasV ? a.Vo + (size_t)K * vplane + o_own : nullptr;
 
   // Complete level kk (its partials, base and bottom-face W are the carries)
   // with the top-face vertical flux, which needs G of the level above.
-  auto complete = [&](int kk, T Gsc, T Guc, T Gvc) {
+  auto complete = [&](T Gsc, T Guc, T Gvc) {
     const T TPh = PPh + (ADV ? (Wb * Gsc) * p_wc : T(0));
     const T TU = PU + (ADV ? ((Wb + Wbp) * Guc) * p_wu : T(0));
     const T bPh = MODE == 0 ? T(0) : pbPh, bU = MODE == 0 ? T(0) : pbU;
     const T oPh = bPh + cdt * TPh, oU = bU + cdt * TU;
-    const unsigned o = (unsigned)kk * plane + o_own;
+    oPhp -= plane;
+    oUp -= plane;
     if (owned) {
-      a.Phio[o] = oPh;
-      a.Uo[o] = oU;
+      *oPhp = oPh;
+      *oUp = oU;
     }
     if (kInc)
       dubar += p_ds * (oU - bU);
@@ -453,7 +465,8 @@ __device__ __forceinline__ void row_segment(const Geom<T>& g, const RowArgs<T>& 
       const T TV = PV + (ADV ? ((Wb + Wbs) * Gvc) * p_wv : T(0));
       const T bV = MODE == 0 ? T(0) : pbV;
       const T oV = bV + cdt * TV;
-      if (owned) a.Vo[(unsigned)kk * vplane + o_own] = oV;
+      oVp -= vplane;
+      if (owned) *oVp = oV;
       if (kInc)
         dvbar += p_ds * (oV - bV);
       else
@@ -538,7 +551,7 @@ __device__ __forceinline__ void row_segment(const Geom<T>& g, const RowArgs<T>& 
     A[11 * NTP] = psi;                    // psi, row j
     A[12 * NTP] = Wt;                     // W at the top face, row j
     // the level below is complete now that G of this level is known
-    if (k + 1 <= K - 1) complete(k + 1, Gsc, Guc, Gvc);
+    if (k + 1 <= K - 1) complete(Gsc, Guc, Gvc);  // level k + 1
     const T wc = r2dsk * rPc, wu = T(0.5) * r2dsk * rPuc, wv = T(0.5) * r2dsk * rPvc;
     row_sync(NTW);
     // every thread is past its reads of this ring slot: fetch level k - R into it
@@ -598,7 +611,7 @@ __device__ __forceinline__ void row_segment(const Geom<T>& g, const RowArgs<T>& 
   }
   if (k == 0) level(0, std::integral_constant<int, 0>{});
   // level 0 has no level above: its top-face flux W_0 G_{-1} is zero
-  complete(0, T(0), T(0), T(0));
+  complete(T(0), T(0), T(0));
   if (owned && a.Ubar_o) {
     if (kInc) {
       ubar = a.Ubar_b[o_own] + (double)dubar;

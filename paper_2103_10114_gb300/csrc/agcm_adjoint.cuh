@@ -114,7 +114,8 @@ struct ColCtx {
   const Geom<T>& g;
   const T* lt = nullptr;  // shared-memory level tables (ST)
   const T *U, *V, *Phi, *yU, *yV, *yPhi;
-  size_t plane, vplane, r2;
+  // element offsets fit 32 bits: nlon * nlat * nlev <= 4e9
+  unsigned plane, vplane, r2;
   int ic, ue, uw, im;
   bool hasS, hasN, nl;
   T rdx, rdy, rady, svS, svN, Pue, Puw, rPc, rPui, rPum, PvS, PvN, rPvS, rPvN;
@@ -132,9 +133,9 @@ struct ColCtx {
                     const ColState<T>& cs, const T* yU_, const T* yV_, const T* yPhi_, int i, int j)
       : g(g_), lt(lt_), U(U_), V(V_), Phi(Phi_), yU(yU_), yV(yV_), yPhi(yPhi_) {
     const int I = g.I, J = g.J;
-    plane = (size_t)J * I;
-    vplane = (size_t)(J - 1) * I;
-    r2 = (size_t)j * I;
+    plane = (unsigned)J * (unsigned)I;
+    vplane = (unsigned)(J - 1) * (unsigned)I;
+    r2 = (unsigned)j * (unsigned)I;
     ic = i;
     hasS = j < J - 1;
     hasN = j > 0;
@@ -148,7 +149,7 @@ struct ColCtx {
     rady = g.rady;
     svS = hasS ? ldg(g.sv + j) : T(0);
     svN = hasN ? ldg(g.sv + j - 1) : T(0);
-    const size_t n = r2 + ic;
+    const unsigned n = r2 + ic;
     Pue = ldg(cs.Pu + r2 + ue);
     Puw = ldg(cs.Pu + r2 + uw);
     rPc = ldg(cs.rP + n);
@@ -167,18 +168,19 @@ struct ColCtx {
   };
   __device__ void level(int k, Lev& v) const {
     const int I = g.I;
-    const T* u = U + (size_t)k * plane + r2;
-    const T* yu = yU + (size_t)k * plane + r2;
-    const T* vv = V + (size_t)k * vplane + r2;
-    const T* yvv = yV + (size_t)k * vplane + r2;
+    const unsigned o3 = (unsigned)k * plane + r2, ov = (unsigned)k * vplane + r2;
+    const T* u = U + o3;
+    const T* yu = yU + o3;
+    const T* vv = V + ov;
+    const T* yvv = yV + ov;
     const T VS = hasS ? ldg(vv + ic) : T(0), VN = hasN ? ldg(vv - I + ic) : T(0);
     const T yVS = hasS ? ldg(yvv + ic) : T(0), yVN = hasN ? ldg(yvv - I + ic) : T(0);
     v.D = (Pue * ldg(u + ue) - Puw * ldg(u + uw)) * rdx + (svS * PvS * VS - svN * PvN * VN) * rdy;
     // the pressure-gradient terms of the U points i - (M+1)/2, i + (M-1)/2
     // and the V points (j-1, i), (j, i) read psi(j, i)
     v.pb = rdx * (ldg(yu + ue) * Pue - ldg(yu + uw) * Puw) + rady * (yVS * PvS - yVN * PvN);
-    v.ph = ldg(Phi + (size_t)k * plane + r2 + ic);
-    v.yx = ldg(yPhi + (size_t)k * plane + r2 + ic);
+    v.ph = ldg(Phi + o3 + ic);
+    v.yx = ldg(yPhi + o3 + ic);
     v.q[0] = v.yx * rPc;
     v.x[0] = v.ph * rPc;
     v.q[1] = ldg(yu + im) * rPum;
@@ -260,7 +262,7 @@ __device__ __forceinline__ ColSums<T> col_exchange(T* red, int G, int gy, int la
 // sums up to level k (qD before it, the others including it), s*: this
 // group's totals, r: the other groups' offsets.
 template <class T, bool ST>
-__device__ __forceinline__ void col_suffix(const ColCtx<T, ST>& c, const AdjCol<T>& o, int k, size_t q3, T D, T B,
+__device__ __forceinline__ void col_suffix(const ColCtx<T, ST>& c, const AdjCol<T>& o, int k, unsigned q3, T D, T B,
                                            T xb, T qD, T qB, T qX, T qA, T sD, T sB, T sX, T sA,
                                            const ColSums<T>& r, T ps) {
   const T ds = c.tab(k, kLds), Hkk = c.tab(k, kLHkk);
@@ -301,7 +303,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? AGCM_COLB : 2) k_adj_col
   __syncthreads();
   const ColCtx<T, true> c(g, lt, U, V, Phi, cs, yU, yV, yPhi, col ? i : 0, j);
   const int kb = min(K, gy * kColL), ke = min(K, kb + kColL);
-  const size_t n = c.r2 + c.ic;
+  const unsigned n = c.r2 + c.ic;
   // ---- walk 1: every level's values into shared memory, and the group sums
   auto vD = [&](int l) -> T& { return lv[(0 * kColL + l) * lstride]; };
   auto vP = [&](int l) -> T& { return lv[(1 * kColL + l) * lstride]; };
@@ -343,7 +345,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? AGCM_COLB : 2) k_adj_col
     for (int l = 0; l < kColL; ++l) {
       const int k = kb + l;
       if (k < ke) {
-        const size_t q3 = (size_t)k * c.plane + n;
+        const unsigned q3 = (unsigned)k * c.plane + n;
         const T D = vD(l), pb = vP(l), ph = vPh(l), yx = vY(l);
         o.aPhi[q3] = c.adj_phi(k, D, pb, ph, yx, Q, pre, arp);
         const T dsk = c.tab(k, kLds);
@@ -385,7 +387,7 @@ __global__ void __launch_bounds__(32 * kColG) k_adj_col_w(Geom<T> g, const T* __
   const ColCtx<T, false> c(g, nullptr, U, V, Phi, cs, yU, yV, yPhi, col ? i : 0, j);
   const int L = (K + kColG - 1) / kColG;
   const int kb = min(K, gy * L), ke = min(K, kb + L);
-  const size_t n = c.r2 + c.ic;
+  const unsigned n = c.r2 + c.ic;
   T s[6] = {0, 0, 0, 0, 0, 0};
   typename ColCtx<T, false>::Lev cv{}, pv{};
   if (kb < ke) {
@@ -411,7 +413,7 @@ __global__ void __launch_bounds__(32 * kColG) k_adj_col_w(Geom<T> g, const T* __
     if (kb > 0) c.level(kb - 1, pv);
     for (int k = kb; k < ke; ++k) {
       c.level(k, cv);
-      const size_t q3 = (size_t)k * c.plane + n;
+      const unsigned q3 = (unsigned)k * c.plane + n;
       o.aPhi[q3] = c.adj_phi(k, cv.D, cv.pb, cv.ph, cv.yx, Q, pre, arp);
       Q += ldg(g.ds + k) * cv.D;
       pre += cv.pb;
@@ -785,8 +787,9 @@ __global__ void __launch_bounds__(kAdjRowB, sizeof(T) == 4 ? AGCM_ADJROWB : 1) k
   const bool active = t < own + 2 * H, owner = t >= H && t < H + own;
   int c = (s0 - H + t) % I;
   if (c < 0) c += I;
-  const size_t plane = (size_t)J * I, vplane = (size_t)(J - 1) * I;
-  const size_t r2 = (size_t)j * I;
+  // element offsets fit 32 bits: nlon * nlat * nlev <= 4e9
+  const unsigned plane = (unsigned)J * (unsigned)I, vplane = (unsigned)(J - 1) * (unsigned)I;
+  const unsigned r2 = (unsigned)j * (unsigned)I;
   // row tables
   const T zf = ldg(g.zf + j), r2A = ldg(g.r2A + j), rdx = ldg(g.rdx + j), f0 = ldg(g.f0 + j),
           cota = ldg(g.cota + j);
@@ -819,7 +822,7 @@ __global__ void __launch_bounds__(kAdjRowB, sizeof(T) == 4 ? AGCM_ADJROWB : 1) k
     T yP0, P0, yU0, U0, yV0, V0, yP1, P1, yU1, U1, yV1, V1, yPm, Pm, yUm, Um, yVm, Vm;
   };
   auto load_raw = [&](int k, Raw& r) {
-    const size_t r3 = (size_t)k * plane + r2 + c, rv = (size_t)k * vplane + r2 + c;
+    const unsigned r3 = (unsigned)k * plane + r2 + c, rv = (unsigned)k * vplane + r2 + c;
     r.yP0 = ldg(yPhi + r3);
     r.P0 = ldg(Phi + r3);
     r.yU0 = ldg(yU + r3);
@@ -845,7 +848,7 @@ __global__ void __launch_bounds__(kAdjRowB, sizeof(T) == 4 ? AGCM_ADJROWB : 1) k
     T psa, psb, psc, pss, Dba, Dbb, Dbc, Dbs, aPh;
   };
   auto load_own = [&](int k, Own& w) {
-    const size_t r3 = (size_t)k * plane + r2;
+    const unsigned r3 = (unsigned)k * plane + r2;
     w.psa = ldg(psi + r3 + a0g);
     w.psb = ldg(psi + r3 + b0g);
     w.psc = ldg(psi + r3 + c);
@@ -877,10 +880,10 @@ __global__ void __launch_bounds__(kAdjRowB, sizeof(T) == 4 ? AGCM_ADJROWB : 1) k
     // load is in flight across it
     T accU = 0, accP = 0, accV = 0;
     if (owner && rmwU) {
-      const size_t q = (size_t)k * plane + r2 + c;
+      const unsigned q = (unsigned)k * plane + r2 + c;
       accU = rmwU[q];
       accP = rmwP[q];
-      if (hasS) accV = rmwV[(size_t)k * vplane + r2 + c];
+      if (hasS) accV = rmwV[(unsigned)k * vplane + r2 + c];
     }
     if (active) {
       T* const q = b + t;
@@ -918,7 +921,7 @@ __global__ void __launch_bounds__(kAdjRowB, sizeof(T) == 4 ? AGCM_ADJROWB : 1) k
     if (owner && k + 1 < K) load_own(k + 1, onxt);
     T Wb = 0, Wbp = 0, Wbs = 0;
     if (owner && k + 1 < K) {
-      const size_t wq = (size_t)(k + 1) * plane + r2;
+      const unsigned wq = (unsigned)(k + 1) * plane + r2;
       Wb = ldg(W + wq + c);
       Wbp = ldg(W + wq + cp);
       Wbs = hasS ? ldg(W + wq + I + c) : T(0);
@@ -927,7 +930,7 @@ __global__ void __launch_bounds__(kAdjRowB, sizeof(T) == 4 ? AGCM_ADJROWB : 1) k
     if (owner) {
       const T* const L = b + t;
       auto A = [&](int arr, int off) { return L[arr * kAdjRowB + off]; };
-      const size_t r3 = (size_t)k * plane + r2, rv = (size_t)k * vplane + r2;
+      const unsigned r3 = (unsigned)k * plane + r2, rv = (unsigned)k * vplane + r2;
       const T r2ds = ldg(g.r2ds + k);
       const T r2dsU = k > 0 ? ldg(g.r2ds + k - 1) : T(0), r2dsD = k + 1 < K ? ldg(g.r2ds + k + 1) : T(0);
       const bool up = k > 0, dn = k + 1 < K;
@@ -964,7 +967,7 @@ __global__ void __launch_bounds__(kAdjRowB, sizeof(T) == 4 ? AGCM_ADJROWB : 1) k
       aPu += aFl * Uc + tPu;
       arPu += aGu * Uc + tRPu;
       {
-        const size_t q = r3 + c;
+        const unsigned q = r3 + c;
         const T v = o.scale * bu;
         if (o.sU) {
           o.oU[q] = v;
@@ -985,7 +988,7 @@ __global__ void __launch_bounds__(kAdjRowB, sizeof(T) == 4 ? AGCM_ADJROWB : 1) k
       const T bp = ocur.aPh + aGs * rPc;
       arP += aGs * Pc + tRP;
       {
-        const size_t q = r3 + c;
+        const unsigned q = r3 + c;
         const T v = o.scale * bp;
         if (o.sU) {
           o.oPhi[q] = v;
@@ -1023,7 +1026,7 @@ __global__ void __launch_bounds__(kAdjRowB, sizeof(T) == 4 ? AGCM_ADJROWB : 1) k
         const T bv = aV + aFt * Pvc + aGv * rPvc;
         aPv += aFt * Vc + tPv;
         arPv += aGv * Vc + tRPv;
-        const size_t q = rv + c;
+        const unsigned q = rv + c;
         const T v = o.scale * bv;
         if (o.sU) {
           o.oV[q] = v;
@@ -1039,7 +1042,7 @@ __global__ void __launch_bounds__(kAdjRowB, sizeof(T) == 4 ? AGCM_ADJROWB : 1) k
     ocur = onxt;
   }
   if (owner) {
-    const size_t n = r2 + c;
+    const unsigned n = r2 + c;
     m.mub[n] = aPu * T(0.5) * rPuc - arPu * T(0.5) * rPuc * rPuc * rPuc;
     m.mvb[n] = hasS ? aPv * T(0.5) * rPvc - arPv * T(0.5) * rPvc * rPvc * rPvc : T(0);
     m.mcb[n] = -arP * T(0.5) * rPc * rPc * rPc;

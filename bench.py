@@ -43,7 +43,7 @@ BYTES_PER_POINT_STEP = {4: 96, 8: 192}  # 24 words: stages read/write 6 + 9 + 9 
 NCU_TRAFFIC = {
     # kernel bracket name: (sha1 of the stage-kernel sources at capture time,
     # DRAM bytes per stage summed over the stage's launches)
-    "k_fused_stage": ("5157b1b93784addc97816fad2c174e916c5ffcfd", 957000000),
+    "k_fused_stage": ("258877acbd97fc4c24f8aec545ab8875feb7f696", 958600000),
 }
 
 # Instruction counters of the dominant kernel (ncu per-opcode counts, this
@@ -52,14 +52,14 @@ NCU_TRAFFIC = {
 # point and stage (fadd + fmul + 2 ffma), thread instructions per point, warp
 # instructions issued per point.
 NCU_OPS = {
-    "k_fused_stage": ("5157b1b93784addc97816fad2c174e916c5ffcfd", 182.9, 358.9, 11.22),
+    "k_fused_stage": ("258877acbd97fc4c24f8aec545ab8875feb7f696", 181.0, 317.1, 9.91),
 }
 
 
 # DRAM traffic of one FP32 adjoint step at 720x360x30 (all its launches: the
 # forward recompute of the two stage states and three adjoint products), from
 # an ncu capture, valid while the kernel sources are the captured ones.
-NCU_ADJ = ("401583f13b6616b2d1545b50f4972059004af20f", 2830007552)
+NCU_ADJ = ("e647064e01eaf600b30301df7dae403c4eeb8f86", 2832253440)
 
 
 def kernel_source_hash(names=("agcm_row.cuh", "agcm_fused.cuh", "agcm_common.cuh")):

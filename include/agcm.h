@@ -205,11 +205,17 @@ int agcm_tendency(agcm_state_t* state, void* tU, void* tV, void* tPhi, void* tpi
 
 /*
  * agcm_step_adjoint — vector-Jacobian product of ONE step at the state x_n
- * currently held by `xn` (not modified): lam_out = (d x_{n+1} / d x_n)^T lam_in.
+ * currently held by `xn` (not modified): lam_out = (d x_{n+1} / d x_n)^T lam_in,
+ * the step being the three-stage scheme over Eq. 1's spatial operator.
  * lam_in[4] / lam_out[4] are caller-owned device buffers {U, V, Phi, pi} of the
- * state's element type; lam_in and lam_out must not alias.  The three stage
- * states are recomputed from x_n.  Exact transpose of the linearised
- * step, hand-written (no automatic differentiation).
+ * state's element type and layout; lam_in and lam_out must not alias
+ * (AGCM_EINVAL when a lam_in buffer is a lam_out buffer).  The stage states are
+ * recomputed from x_n.  Exact transpose of the linearised step, hand-written
+ * (no automatic differentiation): every element of the result is formed by one
+ * thread from the terms whose stencil reads it, so the result is the same bit
+ * for bit on every call.  The first call allocates the state's adjoint
+ * workspace (about ten field-sized arrays; AGCM_ENOMEM if that fails).
+ * Asynchronous on `stream`.
  */
 int agcm_step_adjoint(agcm_state_t* xn, const void* const lam_in[4], void* const lam_out[4], double dt,
                       void* stream);

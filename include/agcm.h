@@ -247,8 +247,10 @@ int agcm_diagnostics(const agcm_state_t* state, agcm_diag_t* out, void* stream);
  * agcm_profile_read synchronises the recorded events and returns, per kernel
  * id 0..agcm_kernel_count()-1, the summed milliseconds and the launch count.
  * The events bracket a whole stage of the stage kernel, which is one launch
- * or two concurrent ones (the stride-1 row band and the other rows): its
- * milliseconds are per stage, its count is of launches.
+ * or several concurrent ones (the row-segment kernel once per stride class,
+ * the column kernel for the rows next to the poles; or the column kernel's
+ * stride-1 row band and the other rows): its milliseconds are per stage, its
+ * count is of launches.
  * ms_total and launches hold at least agcm_kernel_count() entries.
  */
 int agcm_profile_enable(agcm_state_t* state, int enable);
@@ -266,6 +268,16 @@ int agcm_profile_enable(agcm_state_t* state, int enable);
  * run the column kernel.  Other values return AGCM_EINVAL.  Host only.
  */
 int agcm_set_stage_kernel(int choice);
+/*
+ * agcm_state_set_stage_kernel — the same choice for one state only: 1 the
+ * column kernel, 2 the row-segment kernel wherever the rows allow it, 0 (the
+ * default) the process's agcm_set_stage_kernel.  An ensemble of many states
+ * stepped side by side on several streams can run its small members on the
+ * row-segment kernel, which a state alone would not choose (its segments would
+ * not fill the GPU).  Other values or a null state return AGCM_EINVAL.  Host
+ * only; takes effect at the state's next launch.
+ */
+int agcm_state_set_stage_kernel(agcm_state_t* state, int choice);
 int agcm_profile_read(agcm_state_t* state, double* ms_total, int64_t* launches);
 int agcm_kernel_count(void);
 const char* agcm_kernel_name(int id);

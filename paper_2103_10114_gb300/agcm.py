@@ -99,6 +99,7 @@ SIGNATURES = {
     "agcm_kernel_count": (_i, []),
     "agcm_kernel_name": (ctypes.c_char_p, [_i]),
     "agcm_set_stage_kernel": (_i, [_i]),
+    "agcm_state_set_stage_kernel": (_i, [_vp, _i]),
     "agcm_tendency_static": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "agcm_ensemble_create": (_i, [ctypes.POINTER(_vp), _i, ctypes.POINTER(_vp)]),
     "agcm_ensemble_destroy": (_i, [_vp]),
@@ -362,6 +363,11 @@ class State:
         if rc not in (AGCM_OK, AGCM_ENONFINITE):
             check(rc)
         return d
+
+    def set_stage_kernel(self, choice):
+        """agcm_state_set_stage_kernel: 0 the process's choice (default), 1 column
+        kernel, 2 row-segment kernel, for this state only."""
+        check(lib().agcm_state_set_stage_kernel(self._h, int(choice)))
 
     def profile(self, enable=True):
         check(lib().agcm_profile_enable(self._h, 1 if enable else 0))

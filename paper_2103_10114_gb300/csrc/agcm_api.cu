@@ -220,6 +220,7 @@ struct Profiler {
 struct agcm_state {
   Profiler prof;
   const agcm_grid* grid = nullptr;
+  int stage_choice = 0;  // 0: the process's agcm_set_stage_kernel; 1 column; 2 row segments
   int prec = AGCM_FP64;
   size_t esz = 8;
   size_t n3 = 0, nv = 0, n2 = 0;
@@ -545,7 +546,8 @@ template <class T, int MODE, int TERMS = 3>
 int launch_fused(const agcm::Geom<T>& G, const void* const xs[4], const double* ub, const double* vb,
                  const void* const xb[4], void* const out[4], double* ubo, double* vbo, const double* ubb,
                  const double* vbb, double cdt, int* err, cudaStream_t st, cudaStream_t aux = nullptr,
-                 cudaEvent_t evf = nullptr, cudaEvent_t evj = nullptr, int* launched = nullptr) {
+                 cudaEvent_t evf = nullptr, cudaEvent_t evj = nullptr, int* launched = nullptr,
+                 int state_choice = 0) {
   if (launched) *launched = 1;
   const bool fork = aux && evf && evj;
   auto col_launch = [&](auto nl, auto part, int ny, cudaStream_t q) {
@@ -571,7 +573,8 @@ int launch_fused(const agcm::Geom<T>& G, const void* const xs[4], const double* 
     return AGCM_OK;
   };
   auto a16 = [](const void* p) { return ((uintptr_t)p & 15) == 0; };
-  const int choice = g_stage_choice.load(std::memory_order_relaxed);
+  // a state's own choice (agcm_state_set_stage_kernel), else the process's
+  const int choice = state_choice > 0 ? state_choice : g_stage_choice.load(std::memory_order_relaxed);
   bool rowpath = AGCM_ROW_KERNEL && choice != 1 && (choice == 2 || G.rowfill) && G.nk[0] + G.nk[1] + G.nk[2] > 0 &&
                  a16(xs[0]) && a16(xs[1]) && a16(xs[2]);
   if (MODE == 2) rowpath = rowpath && a16(xb[0]) && a16(xb[1]) && a16(xb[2]);
@@ -644,7 +647,7 @@ int fused_stage(agcm_state* s, int in, void* const out[4], int outb, double cdt,
   int rc = launch_fused<T, MODE, TERMS>(G, s->x[in], s->ubar[in], s->vbar[in], s->x[0], out,
                                  outb >= 0 ? s->ubar[outb] : nullptr, outb >= 0 ? s->vbar[outb] : nullptr,
                                  s->ubar[0], s->vbar[0], cdt, s->err, st, s->aux, s->ev_fork, s->ev_join,
-                                 &launched);
+                                 &launched, s->stage_choice);
   s->prof.end(st, launched);
   return rc;
 }
@@ -1191,6 +1194,13 @@ int agcm_kernel_count(void) { return KID_COUNT; }
 int agcm_set_stage_kernel(int choice) {
   if (choice < 0 || choice > 2) return fail(AGCM_EINVAL, "stage kernel choice must be 0, 1 or 2");
   g_stage_choice.store(choice);
+  return AGCM_OK;
+}
+
+int agcm_state_set_stage_kernel(agcm_state_t* s, int choice) {
+  if (!s) return fail(AGCM_EINVAL, "null state");
+  if (choice < 0 || choice > 2) return fail(AGCM_EINVAL, "stage kernel choice must be 0, 1 or 2");
+  s->stage_choice = choice;
   return AGCM_OK;
 }
 

@@ -12,8 +12,12 @@ Two ways to advance the members, both captured whole in one CUDA graph:
 * "streams": each member stepped by the single-state kernel (agcm_step) with
   the members spread round-robin over N CUDA streams, so small members run
   side by side.  The single-state kernel reads its grid tables from the launch
-  parameters and fits in 96 registers, where the persistent kernel, which
-  reads each member's tables through a descriptor, needs 168.
+  parameters and fits in 80-96 registers, where the persistent kernel, which
+  reads each member's tables through a descriptor, needs 168.  "streams-row"
+  does the same with every member on the row-segment stage kernel
+  (agcm_state_set_stage_kernel 2): a small member alone would not fill the
+  GPU with row segments and takes the column kernel, but side by side with
+  the others its row segments are the cheaper work per point.
 
 The best choice depends on the member mix and the GPU, so `autotune` times
 each candidate on the ensemble itself and keeps the fastest (cached per
@@ -47,16 +51,23 @@ class Ensemble:
 
     def configure(self, warps_per_block, blocks_per_sm=0, rows_per_item=1):
         """Persistent launch: (warps per block, blocks per SM, rows per item).
-        Streams: configure("streams", n) steps the members on n streams."""
-        if warps_per_block == "streams":
+        Streams: configure("streams", n) steps the members on n streams, each
+        member on the stage kernel its own grid calls for; configure("streams-row",
+        n) with every member on the row-segment kernel.  Configuring sets the
+        members' stage-kernel choice (agcm_state_set_stage_kernel)."""
+        if warps_per_block in ("streams", "streams-row"):
             import torch
 
             n = int(blocks_per_sm)
             if n < 1:
                 raise ValueError("need at least one stream")
             self._streams = [torch.cuda.Stream() for _ in range(n)]
-            self.shape = ("streams", n)
+            for s in self.states:
+                s.set_stage_kernel(2 if warps_per_block == "streams-row" else 0)
+            self.shape = (warps_per_block, n)
             return
+        for s in self.states:
+            s.set_stage_kernel(0)
         agcm.check(agcm.lib().agcm_ensemble_configure(self._h, int(warps_per_block), int(blocks_per_sm)))
         agcm.check(agcm.lib().agcm_ensemble_tile(self._h, int(rows_per_item)))
         self.shape = (int(warps_per_block), int(blocks_per_sm), int(rows_per_item))
@@ -65,7 +76,7 @@ class Ensemble:
         agcm.check(agcm.lib().agcm_ensemble_set_timeout(self._h, float(seconds), int(test_missing_blocks)))
 
     def step(self, nsteps, dts, stream=None):
-        if self.shape[0] == "streams":
+        if self.shape[0] in ("streams", "streams-row"):
             self._step_streams(nsteps, dts, stream)
             return
         arr = (ctypes.c_double * len(self.states))(*[float(d) for d in dts])
@@ -103,12 +114,16 @@ class Ensemble:
         return (torch.cuda.get_device_name(), tuple((s.grid.nlon, s.grid.nlat, s.grid.nlev, s.precision)
                                                     for s in self.states))
 
-    def autotune(self, dts, steps=2, candidates=None, verbose=False):
+    def autotune(self, dts, steps=2, candidates=None, verbose=False, graph=False):
         """Time each launch shape on this ensemble (the states are restored
-        afterwards) and keep the fastest.  Returns (shape, {shape: ms/step})."""
+        afterwards) and keep the fastest.  Returns (shape, {shape: ms/step}).
+        graph=True times each shape replayed from a CUDA graph of `steps`
+        steps (for an ensemble that will be replayed so: the host's launch
+        cost, which differs between the shapes, is then not part of a step),
+        else called eagerly."""
         import torch
 
-        key = self.signature()
+        key = self.signature() + (bool(graph),)
         if key in _TUNE_CACHE:
             self.configure(*_TUNE_CACHE[key])
             return _TUNE_CACHE[key], {}
@@ -116,6 +131,7 @@ class Ensemble:
             candidates = [(1, b, r) for r in (1, 2, 4) for b in (0, 8, 16)]
             candidates += [(8, b, 1) for b in (0, 2)]
             candidates += [("streams", n) for n in (4, 8, 16)]
+            candidates += [("streams-row", n) for n in (8, 16)]
         saved = [s.store() for s in self.states]
         times = {}
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -123,9 +139,17 @@ class Ensemble:
             self.configure(*shape)
             self.step(1, dts)
             torch.cuda.synchronize()
-            e0.record()
-            self.step(steps, dts)
-            e1.record()
+            if graph:
+                g = self.capture(steps, dts)
+                g.replay()
+                torch.cuda.synchronize()
+                e0.record()
+                g.replay()
+                e1.record()
+            else:
+                e0.record()
+                self.step(steps, dts)
+                e1.record()
             torch.cuda.synchronize()
             self.status()
             times[shape] = e0.elapsed_time(e1) / steps

@@ -144,6 +144,36 @@ def test_row_kernel_launches_one_per_stride_class(grid, stage_kernel):
     s.close()
 
 
+def test_state_stage_kernel_choice_overrides_the_process_one():
+    """agcm_state_set_stage_kernel: a state set to 2 runs the row-segment
+    kernel on a grid too small for the process's default to pick it, a state
+    left at 0 keeps the default, and both agree with each other to rounding."""
+    I, J, K = 64, 32, 6
+    g = agcm.Grid(I, J, K)
+    lu, lv = g.leap()
+    x = inputs.random_state(I, J, K, seed=4)
+    dt = g.dt(100.0)
+    out, launches = {}, {}
+    for choice in (0, 2):
+        s = agcm.State(g, agcm.AGCM_FP32)
+        s.set_stage_kernel(choice)
+        s.load(x)
+        s.profile(True)
+        s.step(2, dt)
+        launches[choice] = s.profile_read()["k_fused_stage"][1]
+        s.profile(False)
+        out[choice] = {f: v.double().cpu().numpy() for f, v in s.store().items()}
+        s.close()
+    assert launches[2] == 6 * _row_kernel_launches(lu, lv, I)
+    band = [j for j in range(1, J - 2) if lu[j] == 1 and lv[j] == 1 and lu[j + 1] == 1]
+    assert launches[0] == 6 * (2 if 0 < len(band) < J else 1)
+    for f in FIELDS:
+        err = np.abs(out[2][f] - out[0][f]).max() / np.abs(out[0][f]).max()
+        assert err <= 1e-5, (f, err)
+    with pytest.raises(agcm.AgcmError):
+        agcm.State(g, agcm.AGCM_FP32).set_stage_kernel(3)
+
+
 @pytest.mark.parametrize("leap", ["ones", "eq7", "none"])
 def test_stage_launch_count_follows_the_stride1_band(leap):
     """A stage is two launches when the grid has a run of interior rows

@@ -118,12 +118,13 @@ def test_barrier_timeout_is_reported_and_context_survives(shape):
     ens.close()
 
 
-def test_autotune_picks_a_shape_and_keeps_state():
+@pytest.mark.parametrize("graph", [False, True], ids=["eager", "graph"])
+def test_autotune_picks_a_shape_and_keeps_state(graph):
     mem = members(agcm.AGCM_FP32)
     ens = Ensemble([m[1] for m in mem])
     dts = [m[3] for m in mem]
     before = [np_state(m[1]) for m in mem]
-    shape, times = ens.autotune(dts, steps=1)
+    shape, times = ens.autotune(dts, steps=1, graph=graph)
     assert shape in times and all(t > 0 for t in times.values())
     after = [np_state(m[1]) for m in mem]
     for a, b in zip(before, after):
@@ -145,7 +146,7 @@ def test_config4_full_mix_sampled_members():
     mem = members(agcm.AGCM_FP32, mix=mix, seed0=100)
     ens = Ensemble([m[1] for m in mem])
     dts = [m[3] for m in mem]
-    ens.autotune(dts, steps=1)
+    ens.autotune(dts, steps=1, graph=True)
     graph = ens.capture(2, dts)
     graph.replay()
     torch.cuda.synchronize()
@@ -154,6 +155,7 @@ def test_config4_full_mix_sampled_members():
         g, s, st, dt = mem[q]
         got = np_state(s)
         alone = agcm.State(g, agcm.AGCM_FP32)
+        alone.set_stage_kernel(2 if ens.shape[0] == "streams-row" else 0)  # the member's stage kernel
         alone.load(st)
         alone.step(2, dt)
         want = np_state(alone)
@@ -171,15 +173,17 @@ def test_config4_full_mix_sampled_members():
     ens.close()
 
 
+@pytest.mark.parametrize("mode", ["streams", "streams-row"])
 @pytest.mark.parametrize("prec", [agcm.AGCM_FP32, agcm.AGCM_FP64])
-def test_streams_mode_equals_single_runs_and_replays(prec):
-    """The streams mode steps every member with the single-state kernel, so
-    each member equals its own run bit for bit, eagerly and from a graph."""
+def test_streams_mode_equals_single_runs_and_replays(prec, mode):
+    """The streams modes step every member with the single-state kernel (in
+    "streams-row" the row-segment kernel), so each member equals its own run
+    on the same kernel bit for bit, eagerly and from a graph."""
     import torch
 
     mem = members(prec)
     ens = Ensemble([m[1] for m in mem])
-    ens.configure("streams", 3)
+    ens.configure(mode, 3)
     dts = [m[3] for m in mem]
     ens.step(2, dts)
     graph = ens.capture(2, dts)
@@ -188,6 +192,7 @@ def test_streams_mode_equals_single_runs_and_replays(prec):
     for g, s, st, dt in mem:
         got = np_state(s)
         alone = agcm.State(g, prec)
+        alone.set_stage_kernel(2 if mode == "streams-row" else 0)
         alone.load(st)
         alone.step(2, dt)
         alone.step(2, dt)

@@ -172,6 +172,35 @@ def test_energy_neutral_on_gpu_full_size():
     assert abs(np.sum(A[:, None] * t["pi"])) <= 1e-13 * np.sum(A[:, None] * np.abs(t["pi"]))
 
 
+@pytest.mark.parametrize("prec", [agcm.AGCM_FP64, agcm.AGCM_FP32], ids=["fp64", "fp32"])
+def test_stage_kernels_are_deterministic(prec, stage_kernel):
+    """Every output element of a stage has one writer and every read is
+    ordered by the kernel's barriers, so the tendency and a step are the same
+    bit for bit on fresh states; 720 x 360 x 30 spans every stride class and
+    the polar rows, with several waves of CTAs."""
+    import torch
+
+    I, J, K = 720, 360, 30
+    st = inputs.baroclinic_jet(I, J, K, seed=5, noise=1e-2, terrain_seed=2)
+    g = agcm.Grid(I, J, K, phis=st["phis"])
+    dt = g.dt(100.0)
+    ref = None
+    for _ in range(3):
+        s = agcm.State(g, prec)
+        s.load(st)
+        t = {f: v.clone() for f, v in s.tendency().items()}
+        s.step(2, dt)
+        x = s.store()
+        torch.cuda.synchronize()
+        if ref is None:
+            ref = (t, x)
+        else:
+            for f in FIELDS:
+                assert torch.equal(t[f], ref[0][f]), ("tendency", f)
+                assert torch.equal(x[f], ref[1][f]), ("step", f)
+        s.close()
+
+
 def test_full_size_one_step_fp32():
     """The bench workload itself (1440 x 720 x 30, FP32 with FP64 column sums,
     the same launch path as bench.py): one step against the FP64 oracle."""

@@ -160,6 +160,25 @@ struct ColCtx {
     rPvS = hasS ? ldg(cs.rPv + n) : T(0);
     rPvN = hasN ? ldg(cs.rPv + n - I) : T(0);
   }
+  // an L2 prefetch of the rows a level reads (no registers held: the level
+  // is loaded one level later)
+  __device__ void prefetch(int k) const {
+    const unsigned o3 = (unsigned)k * plane + r2 + ic, ov = (unsigned)k * vplane + r2 + ic;
+    const int I = g.I;
+    auto pf = [](const T* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); };
+    pf(U + o3);
+    pf(yU + o3);
+    pf(Phi + o3);
+    pf(yPhi + o3);
+    if (hasS) {
+      pf(V + ov);
+      pf(yV + ov);
+    }
+    if (hasN) {
+      pf(V + ov - I);
+      pf(yV + ov - I);
+    }
+  }
   // the values of one level: D, the adjoint of psi, Phi, ybar_Phi and the
   // products y / P, x / P of the five points whose vertical advection holds
   // W(j, i): Phi (j, i), U (j, i-1), U (j, i), V (j-1, i), V (j, i)
@@ -317,6 +336,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? AGCM_COLB : 2) k_adj_col
   for (int l = 0; l < kColL; ++l) {
     const int k = kb + l;
     if (k < ke) {
+      if (k + 1 < ke) c.prefetch(k + 1);
       c.level(k, cv);
       const T aw = k > 0 ? c.adj_w(k, cv, pv) : T(0);
       vD(l) = cv.D;

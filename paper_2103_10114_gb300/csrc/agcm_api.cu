@@ -1268,9 +1268,10 @@ int ensure_adj(agcm_state* s) {
 }
 
 // out = (accumulate ? out : 0) + scale * J(x)^T y, J the Jacobian of T at x;
-// with sum != nullptr also sum += scale * J(x)^T y.  Four launches, no
-// atomics and no zeroing: the P family, the fused column pass (phase B at x
-// and its transpose), the gathered adjoint of every point, the adjoint of pi.
+// with sum != nullptr also sum += scale * J(x)^T y.  No atomics and no
+// zeroing: the P family, the column pass (phase B at x and its transpose),
+// the gathered adjoint of every point (row segments, and the rows past their
+// halo on the second stream), the adjoint of pi.
 template <class T>
 int vjp(agcm_state* s, void* const x[4], const void* const y[4], void* const out[4], double scale, int accumulate,
         cudaStream_t st, void* const* sum = nullptr) {

@@ -462,7 +462,8 @@ __global__ void __launch_bounds__(32 * kColG) k_adj_col_w(Geom<T> g, const T* __
 template <class T>
 struct AdjOut {
   T *oU, *oV, *oPhi, *opi;  // out = (accumulate ? out : 0) + scale * J^T ybar
-  T *sU, *sV, *sPhi, *spi;  // sum += scale * J^T ybar (when sU != nullptr)
+  T *sU, *sV, *sPhi, *spi;  // sum = sum_in + scale * J^T ybar (when sU != nullptr)
+  const T *rU, *rV, *rPhi, *rpi;  // sum_in: the sum itself, or another array
   T scale;
   int accumulate;
 };
@@ -627,7 +628,7 @@ __global__ void __launch_bounds__(kAdjTileX* kAdjTileY, 4) k_adj_gather(
       const size_t q = r3 + i;
       const T v = o.scale * bu;
       o.oU[q] = (o.accumulate ? o.oU[q] : T(0)) + v;
-      if (o.sU) o.sU[q] += v;
+      if (o.sU) o.sU[q] = o.rU[q] + v;
     }
     // ---------------- Phi point (j, i)
     // adjoint of G^s(j, i): zonal pairs (i - M, i), (i, i + M) with face
@@ -652,7 +653,7 @@ __global__ void __launch_bounds__(kAdjTileX* kAdjTileY, 4) k_adj_gather(
       const size_t q = r3 + i;
       const T v = o.scale * bp;
       o.oPhi[q] = (o.accumulate ? o.oPhi[q] : T(0)) + v;
-      if (o.sU) o.sPhi[q] += v;
+      if (o.sU) o.sPhi[q] = o.rPhi[q] + v;
     }
     // ---------------- V point (j, i)
     if (hasS) {
@@ -704,7 +705,7 @@ __global__ void __launch_bounds__(kAdjTileX* kAdjTileY, 4) k_adj_gather(
       const size_t q = rv + i;
       const T v = o.scale * bv;
       o.oV[q] = (o.accumulate ? o.oV[q] : T(0)) + v;
-      if (o.sU) o.sV[q] += v;
+      if (o.sU) o.sV[q] = o.rV[q] + v;
     }
   }
   // P^u = sqrt(m^u): dP^u/dm^u = 1/(2 P^u), d(1/P^u)/dm^u = -1/(2 P^u^3)
@@ -885,9 +886,9 @@ __global__ void __launch_bounds__(kAdjRowB, sizeof(T) == 4 ? AGCM_ADJROWB : 1) k
   if (owner) load_own(0, ocur);
   // the array the owner reads back and adds to: the stage sum, or the
   // output itself when accumulating
-  T* const rmwU = o.sU ? o.sU : (o.accumulate ? o.oU : nullptr);
-  T* const rmwP = o.sU ? o.sPhi : (o.accumulate ? o.oPhi : nullptr);
-  T* const rmwV = o.sU ? o.sV : (o.accumulate ? o.oV : nullptr);
+  const T* const rmwU = o.sU ? o.rU : (o.accumulate ? o.oU : nullptr);
+  const T* const rmwP = o.sU ? o.rPhi : (o.accumulate ? o.oPhi : nullptr);
+  const T* const rmwV = o.sU ? o.rV : (o.accumulate ? o.oV : nullptr);
   // own column at level k-1 (row j, V row j)
   T yPp = 0, Pp = 0, yUp = 0, Up = 0, yVp = 0, Vp = 0;
   // W at level k (rows j, j+1; columns i, i+1), loaded one level ahead
@@ -1083,7 +1084,7 @@ __global__ void __launch_bounds__(256) k_adj_colstate(Geom<T> g, AdjM<T> m, cons
   if (j > 0) mb += T(0.5) * m.mvb[n - I];
   const T v = o.scale * (aPiD[n] + mb);
   o.opi[n] = (o.accumulate ? o.opi[n] : T(0)) + v;
-  if (o.spi) o.spi[n] += v;
+  if (o.spi) o.spi[n] = o.rpi[n] + v;
 }
 
 }  // namespace agcm

@@ -1268,13 +1268,15 @@ int ensure_adj(agcm_state* s) {
 }
 
 // out = (accumulate ? out : 0) + scale * J(x)^T y, J the Jacobian of T at x;
-// with sum != nullptr also sum += scale * J(x)^T y.  No atomics and no
+// with sum != nullptr also sum = sum_in + scale * J(x)^T y (sum_in defaults
+// to sum itself).  No atomics and no
 // zeroing: the P family, the column pass (phase B at x and its transpose),
 // the gathered adjoint of every point (row segments, and the rows past their
 // halo on the second stream), the adjoint of pi.
 template <class T>
 int vjp(agcm_state* s, void* const x[4], const void* const y[4], void* const out[4], double scale, int accumulate,
-        cudaStream_t st, void* const* sum = nullptr) {
+        cudaStream_t st, void* const* sum = nullptr, const void* const* sum_in = nullptr) {
+  if (!sum_in) sum_in = sum;
   const agcm::Geom<T>& G = geom_of<T>(s);
   const size_t n2 = s->n2;
   agcm::ColState<T> cs{(T*)s->col[0], (T*)s->col[1], (T*)s->col[2], (T*)s->col[3], (T*)s->col[4], (T*)s->col[5]};
@@ -1305,7 +1307,10 @@ int vjp(agcm_state* s, void* const x[4], const void* const y[4], void* const out
   const agcm::AdjM<T> m{(T*)s->adj2[2], (T*)s->adj2[3], (T*)s->adj2[4]};
   const agcm::AdjOut<T> o{(T*)out[0], (T*)out[1], (T*)out[2], (T*)out[3],
                           sum ? (T*)sum[0] : nullptr, sum ? (T*)sum[1] : nullptr,
-                          sum ? (T*)sum[2] : nullptr, sum ? (T*)sum[3] : nullptr, (T)scale, accumulate};
+                          sum ? (T*)sum[2] : nullptr, sum ? (T*)sum[3] : nullptr,
+                          sum ? (const T*)sum_in[0] : nullptr, sum ? (const T*)sum_in[1] : nullptr,
+                          sum ? (const T*)sum_in[2] : nullptr, sum ? (const T*)sum_in[3] : nullptr, (T)scale,
+                          accumulate};
   s->prof.begin(KID_ADJ_GATHER, st);
   // the rows of the L1 form run on the state's second stream beside the
   // row-segment kernel (they write other rows)
@@ -1360,13 +1365,11 @@ int adjoint_step(agcm_state* s, const void* const lam_in[4], void* const lam_out
   if ((rc = ensure_bar<T>(s, st))) return rc;
   if ((rc = fused_stage<T, 1>(s, 0, s->x[1], 1, 0.5 * dt, st))) return rc;
   if ((rc = fused_stage<T, 2>(s, 1, s->x[2], 2, 0.5 * dt, st))) return rc;
-  const size_t n[4] = {s->n3, s->nv, s->n3, s->n2};
-  for (int f = 0; f < 4; ++f)
-    if (n[f]) CUDA_TRY(cudaMemcpyAsync(lam_out[f], lam_in[f], n[f] * s->esz, cudaMemcpyDeviceToDevice, st));
   void* const* mu2 = s->mu[0];
   void* const* mu1 = s->mu[1];
-  // each product also adds itself to lam_out (no separate accumulation pass)
-  if ((rc = vjp<T>(s, s->x[2], lam_in, mu2, dt, 0, st, lam_out))) return rc;
+  // each product also adds itself to lam_out (no separate accumulation
+  // pass); the first forms lam_out = lam_in + mu2 (no copy of lam_in)
+  if ((rc = vjp<T>(s, s->x[2], lam_in, mu2, dt, 0, st, lam_out, lam_in))) return rc;
   if ((rc = vjp<T>(s, s->x[1], mu2, mu1, 0.5 * dt, 0, st, lam_out))) return rc;
   return vjp<T>(s, s->x[0], mu1, lam_out, 0.5 * dt, 1, st);
 }

@@ -217,6 +217,8 @@ struct Profiler {
   }
 };
 
+constexpr int kSide = 3;  // side streams of a state
+
 struct agcm_state {
   Profiler prof;
   const agcm_grid* grid = nullptr;
@@ -239,10 +241,11 @@ struct agcm_state {
   // diagnostics partials
   double* diag = nullptr;
   int* err = nullptr;  // device status word: AGCM_ETIMEOUT if a bounded wait gave up
-  // the stage kernel's second launch (the stride-1 band) runs on aux, forked
-  // from and joined to the caller's stream by the two events
-  cudaStream_t aux = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // side streams for the launches of a stage (and of an adjoint product) that
+  // run beside the one on the caller's stream: forked from it by ev_fork,
+  // joined to it by ev_join[q]
+  cudaStream_t aux[kSide] = {};
+  cudaEvent_t ev_fork = nullptr, ev_join[kSide] = {};
   std::vector<void*> owned;
   // adjoint workspace (allocated on the first agcm_step_adjoint call)
   bool adj_ready = false;
@@ -545,8 +548,8 @@ int ensure_bar(agcm_state* s, cudaStream_t st) {
 template <class T, int MODE, int TERMS = 3>
 int launch_fused(const agcm::Geom<T>& G, const void* const xs[4], const double* ub, const double* vb,
                  const void* const xb[4], void* const out[4], double* ubo, double* vbo, const double* ubb,
-                 const double* vbb, double cdt, int* err, cudaStream_t st, cudaStream_t aux = nullptr,
-                 cudaEvent_t evf = nullptr, cudaEvent_t evj = nullptr, int* launched = nullptr,
+                 const double* vbb, double cdt, int* err, cudaStream_t st, const cudaStream_t* aux = nullptr,
+                 cudaEvent_t evf = nullptr, const cudaEvent_t* evj = nullptr, int* launched = nullptr,
                  int state_choice = 0) {
   if (launched) *launched = 1;
   const bool fork = aux && evf && evj;
@@ -558,16 +561,16 @@ int launch_fused(const agcm::Geom<T>& G, const void* const xs[4], const double* 
             (const T*)xb[1], (const T*)xb[2], (const T*)xb[3], (T*)out[0], (T*)out[1], (T*)out[2], (T*)out[3],
             ubo, vbo, ubb, vbb, (T)cdt);
   };
-  auto two = [&](auto first, auto second) -> int {  // first on aux (forked), second on st
+  auto two = [&](auto first, auto second) -> int {  // first on aux[0] (forked), second on st
     if (fork) {
       CUDA_TRY(cudaEventRecord(evf, st));
-      CUDA_TRY(cudaStreamWaitEvent(aux, evf, 0));
+      CUDA_TRY(cudaStreamWaitEvent(aux[0], evf, 0));
     }
-    first(fork ? aux : st);
+    first(fork ? aux[0] : st);
     second(st);
     if (fork) {
-      CUDA_TRY(cudaEventRecord(evj, aux));
-      CUDA_TRY(cudaStreamWaitEvent(st, evj, 0));
+      CUDA_TRY(cudaEventRecord(evj[0], aux[0]));
+      CUDA_TRY(cudaStreamWaitEvent(st, evj[0], 0));
     }
     if (launched) *launched = 2;
     return AGCM_OK;
@@ -601,20 +604,32 @@ int launch_fused(const agcm::Geom<T>& G, const void* const xs[4], const double* 
         ++nlaunch;
         return AGCM_OK;
       };
-      // the stride-1 rows and the column-kernel rows on the second stream,
-      // the stride-3 and other rows on st
-      int rc = two(
-          [&](cudaStream_t q) {
-            cls_go(std::integral_constant<int, 1>{}, 0, q);
-            if (G.nrowc > 0) {
-              col_launch(nl, std::integral_constant<int, 3>{}, G.nrowc, q);
-              ++nlaunch;
-            }
-          },
-          [&](cudaStream_t q) {
-            cls_go(std::integral_constant<int, 3>{}, 1, q);
-            cls_go(std::integral_constant<int, 0>{}, 2, q);
-          });
+      // the launches run side by side: the stride-1 rows on st, the rows
+      // next to the poles (column kernel) and the other two classes each on
+      // a side stream (a launch of less than a wave then no longer waits for
+      // another's last wave).  They are issued longest block first (the
+      // column kernel's level walk, then the classes with the widest halos),
+      // so that the shortest blocks fill the last wave.
+      const bool side[kSide] = {G.nrowc > 0, G.nk[1] > 0, G.nk[2] > 0};
+      if (fork) {
+        CUDA_TRY(cudaEventRecord(evf, st));
+        for (int q = 0; q < kSide; ++q)
+          if (side[q]) CUDA_TRY(cudaStreamWaitEvent(aux[q], evf, 0));
+      }
+      if (G.nrowc > 0) {
+        col_launch(nl, std::integral_constant<int, 3>{}, G.nrowc, fork ? aux[0] : st);
+        ++nlaunch;
+      }
+      int rc = cls_go(std::integral_constant<int, 0>{}, 2, fork ? aux[2] : st);
+      if (!rc) rc = cls_go(std::integral_constant<int, 3>{}, 1, fork ? aux[1] : st);
+      if (!rc) rc = cls_go(std::integral_constant<int, 1>{}, 0, st);
+      if (fork) {  // joined whatever rc says, so that no side stream is left forked
+        for (int q = 0; q < kSide; ++q)
+          if (side[q]) {
+            CUDA_TRY(cudaEventRecord(evj[q], aux[q]));
+            CUDA_TRY(cudaStreamWaitEvent(st, evj[q], 0));
+          }
+      }
       if (rc) return rc;
       if (launched) *launched = nlaunch;
     } else {
@@ -948,11 +963,14 @@ int agcm_grid_dt(const agcm_grid_t* g, double umax, double* dt) {
 }
 
 static void release_streams(agcm_state* s) {
-  if (s->ev_join) cudaEventDestroy(s->ev_join);
+  for (int q = 0; q < kSide; ++q) {
+    if (s->ev_join[q]) cudaEventDestroy(s->ev_join[q]);
+    if (s->aux[q]) cudaStreamDestroy(s->aux[q]);
+    s->ev_join[q] = nullptr;
+    s->aux[q] = nullptr;
+  }
   if (s->ev_fork) cudaEventDestroy(s->ev_fork);
-  if (s->aux) cudaStreamDestroy(s->aux);
-  s->ev_join = s->ev_fork = nullptr;
-  s->aux = nullptr;
+  s->ev_fork = nullptr;
 }
 
 int agcm_state_create(const agcm_grid_t* g, int precision, int nmembers, agcm_state_t** out) {
@@ -1000,10 +1018,17 @@ int agcm_state_create(const agcm_grid_t* g, int precision, int nmembers, agcm_st
       size_t n = f == 1 ? std::max<size_t>(s->nv, 1) : (f == 3 ? s->n2 : s->n3);
       cudaMemset(s->x[c][f], 0, n * s->esz);
     }
-  if (cudaStreamCreateWithFlags(&s->aux, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming) != cudaSuccess ||
-      cudaDeviceSynchronize() != cudaSuccess) {
+  // side stream priorities: the rows next to the poles and the stride class
+  // with the widest halos (the longest blocks) first, then the stride-3
+  // class; the stride-1 class runs on the caller's stream
+  int prio_least = 0, prio_greatest = 0;
+  bool side_ok = cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+  const int prio[kSide] = {prio_greatest, (prio_least + prio_greatest) / 2, prio_greatest};
+  for (int q = 0; q < kSide && side_ok; ++q)
+    side_ok = cudaStreamCreateWithPriority(&s->aux[q], cudaStreamNonBlocking, prio[q]) == cudaSuccess &&
+              cudaEventCreateWithFlags(&s->ev_join[q], cudaEventDisableTiming) == cudaSuccess;
+  if (!side_ok || cudaDeviceSynchronize() != cudaSuccess) {
     const cudaError_t e = cudaGetLastError();
     release_streams(s);
     for (void* p : s->owned) dev_free(p);
@@ -1314,13 +1339,13 @@ int vjp(agcm_state* s, void* const x[4], const void* const y[4], void* const out
   s->prof.begin(KID_ADJ_GATHER, st);
   // the rows of the L1 form run on the state's second stream beside the
   // row-segment kernel (they write other rows)
-  const bool fork = s->n_adj_items > 0 && s->n_adj_rows > 0 && s->aux;
+  const bool fork = s->n_adj_items > 0 && s->n_adj_rows > 0 && s->aux[0];
   if (fork) {
     CUDA_TRY(cudaEventRecord(s->ev_fork, st));
-    CUDA_TRY(cudaStreamWaitEvent(s->aux, s->ev_fork, 0));
+    CUDA_TRY(cudaStreamWaitEvent(s->aux[0], s->ev_fork, 0));
   }
   if (s->n_adj_rows > 0) {
-    cudaStream_t q = fork ? s->aux : st;
+    cudaStream_t q = fork ? s->aux[0] : st;
     const int nch = (G.K + agcm::kAdjLevChunk - 1) / agcm::kAdjLevChunk;
     const dim3 agrid((unsigned)((G.I + agcm::kAdjTileX - 1) / agcm::kAdjTileX),
                      (unsigned)((s->n_adj_rows + agcm::kAdjTileY - 1) / agcm::kAdjTileY), (unsigned)nch);
@@ -1344,8 +1369,8 @@ int vjp(agcm_state* s, void* const x[4], const void* const y[4], void* const out
         (const T*)y[2], m, o);
   }
   if (fork) {
-    CUDA_TRY(cudaEventRecord(s->ev_join, s->aux));
-    CUDA_TRY(cudaStreamWaitEvent(st, s->ev_join, 0));
+    CUDA_TRY(cudaEventRecord(s->ev_join[0], s->aux[0]));
+    CUDA_TRY(cudaStreamWaitEvent(st, s->ev_join[0], 0));
   }
   s->prof.end(st);
   s->prof.begin(KID_ADJ_COLSTATE, st);

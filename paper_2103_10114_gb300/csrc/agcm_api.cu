@@ -537,11 +537,12 @@ int ensure_bar(agcm_state* s, cudaStream_t st) {
 // run the column kernel (agcm_fused.cuh, PART 3).  Grids or buffers the
 // row-segment kernel cannot take run the column kernel on every row, as the
 // stride-1 band (PART 2, specialised body) and the other rows (PART 1).
-// Given aux, evf and evj (a second stream and two events), the smaller launch
-// runs on aux, forked from st after everything already queued there and
-// joined back before st continues, so the two launches overlap; without them
-// they run one after the other on st.  *launched (optional) receives the
-// number of kernel launches made.
+// Given aux, evf and evj (kSide side streams, a fork event and one join event
+// per side stream), launches other than the first run on side streams,
+// forked from st after everything already queued there and joined back
+// before st continues, so they overlap; without them they run one after the
+// other on st.  *launched (optional) receives the number of kernel launches
+// made.
 #ifndef AGCM_ROW_KERNEL
 #define AGCM_ROW_KERNEL 1
 #endif

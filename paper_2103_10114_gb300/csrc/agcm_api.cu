@@ -217,7 +217,7 @@ struct Profiler {
   }
 };
 
-constexpr int kSide = 3;  // side streams of a state
+constexpr int kSide = 5;  // side streams of a state
 
 struct agcm_state {
   Profiler prof;
@@ -288,10 +288,11 @@ inline void leap1_band(const agcm_grid* g, int* lo, int* hi) {
 // Work items of the row-segment stage kernel, j << 8 | segment, for every row
 // whose halo leaves at least half of a CTA to owned columns (the grid's rows
 // must be 16-byte aligned, i.e. nlon % 4 == 0), in three classes: rows whose
-// strides Mu_j, Mv_j, Mu_{j+1} are all 1, all 3, and the others (nk[c] items
-// each, listed in that order); and the rows left to the column kernel.
-inline void row_lists(const agcm_grid* g, std::vector<int>* rowk, std::vector<int>* rowc, int nk[3]) {
-  std::vector<int> cls[3];
+// strides Mu_j, Mv_j, Mu_{j+1} all equal kRowClsM[c] (1, 3, 5, 7), and the
+// others (nk[c] items each, listed in that order); and the rows left to the
+// column kernel.
+inline void row_lists(const agcm_grid* g, std::vector<int>* rowk, std::vector<int>* rowc, int nk[agcm::kRowCls]) {
+  std::vector<int> cls[agcm::kRowCls];
   rowc->clear();
   for (int j = 0; j < g->J; ++j) {
     const bool hv = j < g->J - 1;
@@ -301,7 +302,10 @@ inline void row_lists(const agcm_grid* g, std::vector<int>* rowk, std::vector<in
     agcm::row_segments(g->I, H, agcm::kRowB, &n, &S);
     if (g->I % 4 == 0 && n > 0 && n < 256) {
       // the last row has no V row: always the general class
-      const int c = (hv && Mu == Mv && Mu == M1 && (Mu == 1 || Mu == 3)) ? (Mu == 1 ? 0 : 1) : 2;
+      int c = agcm::kRowCls - 1;
+      if (hv && Mu == Mv && Mu == M1)
+        for (int q = 0; q + 1 < agcm::kRowCls; ++q)
+          if (Mu == agcm::kRowClsM[q]) c = q;
       for (int q = 0; q < n; ++q)
         if (q * S < g->I) cls[c].push_back(j << 8 | q);
     } else {
@@ -309,7 +313,7 @@ inline void row_lists(const agcm_grid* g, std::vector<int>* rowk, std::vector<in
     }
   }
   rowk->clear();
-  for (int c = 0; c < 3; ++c) {
+  for (int c = 0; c < agcm::kRowCls; ++c) {
     nk[c] = (int)cls[c].size();
     rowk->insert(rowk->end(), cls[c].begin(), cls[c].end());
   }
@@ -399,7 +403,7 @@ int upload_geom(const agcm_grid* g, void** blob_out, agcm::Geom<T>* geom_out) {
   size_t o_rt0 = putT(rt0pit), o_pit = putT(g->pit);
   size_t o_bu = putI(filtU), o_bv = putI(filtV);
   std::vector<int> rowk, rowc;
-  int nk[3];
+  int nk[agcm::kRowCls];
   row_lists(g, &rowk, &rowc, nk);
   const int nrowc = (int)rowc.size();
   rowk.push_back(0);
@@ -452,9 +456,10 @@ int upload_geom(const agcm_grid* g, void** blob_out, agcm::Geom<T>* geom_out) {
   G.adl = (T)(kA * g->dlam);
   G.rowk = (const int*)(base + o_rk);
   G.rowc = (const int*)(base + o_rc);
-  for (int c = 0; c < 3; ++c) G.nk[c] = nk[c];
+  long long nitems = 0;
+  for (int c = 0; c < agcm::kRowCls; ++c) nitems += G.nk[c] = nk[c];
   G.nrowc = nrowc;
-  G.rowfill = rows_fill_device((long long)nk[0] + nk[1] + nk[2]);
+  G.rowfill = rows_fill_device(nitems);
   *blob_out = d;
   *geom_out = G;
   return AGCM_OK;
@@ -579,7 +584,9 @@ int launch_fused(const agcm::Geom<T>& G, const void* const xs[4], const double* 
   auto a16 = [](const void* p) { return ((uintptr_t)p & 15) == 0; };
   // a state's own choice (agcm_state_set_stage_kernel), else the process's
   const int choice = state_choice > 0 ? state_choice : g_stage_choice.load(std::memory_order_relaxed);
-  bool rowpath = AGCM_ROW_KERNEL && choice != 1 && (choice == 2 || G.rowfill) && G.nk[0] + G.nk[1] + G.nk[2] > 0 &&
+  int nitems = 0;
+  for (int c = 0; c < agcm::kRowCls; ++c) nitems += G.nk[c];
+  bool rowpath = AGCM_ROW_KERNEL && choice != 1 && (choice == 2 || G.rowfill) && nitems > 0 &&
                  a16(xs[0]) && a16(xs[1]) && a16(xs[2]);
   if (MODE == 2) rowpath = rowpath && a16(xb[0]) && a16(xb[1]) && a16(xb[2]);
   const size_t smem = agcm::row_smem_bytes<T>(agcm::kRowB, G.K);
@@ -590,9 +597,12 @@ int launch_fused(const agcm::Geom<T>& G, const void* const xs[4], const double* 
                           (const T*)xb[0], (const T*)xb[1], (const T*)xb[2], (const T*)xb[3], (T*)out[0],
                           (T*)out[1], (T*)out[2], (T*)out[3], ubo, vbo, ubb, vbb, (T)cdt, G.rowk, err};
       int nlaunch = 0;
-      // one launch per stride class: class c takes items [b, b + nk[c])
-      auto cls_go = [&](auto mc, int c, cudaStream_t q) -> int {
-        if (G.nk[c] == 0) return AGCM_OK;
+      // one launch per stride class, or one over classes [c0, c1) (the
+      // body for any strides); class c's items follow those of the classes before it
+      auto cls_go = [&](auto mc, int c0, int c1, cudaStream_t q) -> int {
+        int off = 0, n = 0;
+        for (int c = 0; c < c1; ++c) (c < c0 ? off : n) += G.nk[c];
+        if (n == 0) return AGCM_OK;
         auto kern = agcm::k_row_stage<T, MODE, TERMS, decltype(nl)::value, decltype(mc)::value>;
         static std::atomic<size_t> attr{0};  // per instantiation: the size set so far
         if (attr.load() < smem) {
@@ -600,18 +610,26 @@ int launch_fused(const agcm::Geom<T>& G, const void* const xs[4], const double* 
           attr.store(smem);
         }
         agcm::RowArgs<T> rc = ra;
-        rc.rows = G.rowk + (c > 0 ? G.nk[0] : 0) + (c > 1 ? G.nk[1] : 0);
-        kern<<<(unsigned)G.nk[c], agcm::kRowB, smem, q>>>(G, rc);
+        rc.rows = G.rowk + off;
+        kern<<<(unsigned)n, agcm::kRowB, smem, q>>>(G, rc);
         ++nlaunch;
         return AGCM_OK;
       };
       // the launches run side by side: the stride-1 rows on st, the rows
-      // next to the poles (column kernel) and the other two classes each on
-      // a side stream (a launch of less than a wave then no longer waits for
-      // another's last wave).  They are issued longest block first (the
-      // column kernel's level walk, then the classes with the widest halos),
-      // so that the shortest blocks fill the last wave.
-      const bool side[kSide] = {G.nrowc > 0, G.nk[1] > 0, G.nk[2] > 0};
+      // next to the poles (column kernel), the stride-3, 5 and 7 rows and
+      // the other rows each on a side stream (a launch of less than a
+      // wave then no longer waits for another's last wave).  They are issued
+      // longest block first (the column kernel's level walk, then the rows
+      // with the widest halos), and the side streams' priorities keep that
+      // order, so that the shortest blocks fill the last wave.  The stride-5
+      // and 7 classes have bodies of their own in the stages of a step; the
+      // tendency and the split term groups take them with the other rows.
+      constexpr bool kSpec = MODE != 0 && TERMS == 3;
+      constexpr int cAny = agcm::kRowCls - 1;
+      const int cOther = kSpec ? cAny : 2;
+      int nOther = 0;
+      for (int c = cOther; c < agcm::kRowCls; ++c) nOther += G.nk[c];
+      const bool side[kSide] = {G.nrowc > 0, G.nk[1] > 0, nOther > 0, kSpec && G.nk[2] > 0, kSpec && G.nk[3] > 0};
       if (fork) {
         CUDA_TRY(cudaEventRecord(evf, st));
         for (int q = 0; q < kSide; ++q)
@@ -621,9 +639,13 @@ int launch_fused(const agcm::Geom<T>& G, const void* const xs[4], const double* 
         col_launch(nl, std::integral_constant<int, 3>{}, G.nrowc, fork ? aux[0] : st);
         ++nlaunch;
       }
-      int rc = cls_go(std::integral_constant<int, 0>{}, 2, fork ? aux[2] : st);
-      if (!rc) rc = cls_go(std::integral_constant<int, 3>{}, 1, fork ? aux[1] : st);
-      if (!rc) rc = cls_go(std::integral_constant<int, 1>{}, 0, st);
+      int rc = cls_go(std::integral_constant<int, 0>{}, cOther, agcm::kRowCls, fork ? aux[2] : st);
+      if (!rc) rc = cls_go(std::integral_constant<int, 3>{}, 1, 2, fork ? aux[1] : st);
+      if constexpr (kSpec) {
+        if (!rc) rc = cls_go(std::integral_constant<int, 7>{}, 3, 4, fork ? aux[4] : st);
+        if (!rc) rc = cls_go(std::integral_constant<int, 5>{}, 2, 3, fork ? aux[3] : st);
+      }
+      if (!rc) rc = cls_go(std::integral_constant<int, 1>{}, 0, 1, st);
       if (fork) {  // joined whatever rc says, so that no side stream is left forked
         for (int q = 0; q < kSide; ++q)
           if (side[q]) {
@@ -1019,13 +1041,14 @@ int agcm_state_create(const agcm_grid_t* g, int precision, int nmembers, agcm_st
       size_t n = f == 1 ? std::max<size_t>(s->nv, 1) : (f == 3 ? s->n2 : s->n3);
       cudaMemset(s->x[c][f], 0, n * s->esz);
     }
-  // side stream priorities: the rows next to the poles and the stride class
-  // with the widest halos (the longest blocks) first, then the stride-3
-  // class; the stride-1 class runs on the caller's stream
+  // side stream priorities: the rows next to the poles and the rows of any
+  // strides (the widest halos, the longest blocks) first, then the stride-3,
+  // 5 and 7 classes; the stride-1 class runs on the caller's stream
   int prio_least = 0, prio_greatest = 0;
   bool side_ok = cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest) == cudaSuccess &&
                  cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming) == cudaSuccess;
-  const int prio[kSide] = {prio_greatest, (prio_least + prio_greatest) / 2, prio_greatest};
+  const int prio_mid = (prio_least + prio_greatest) / 2;
+  const int prio[kSide] = {prio_greatest, prio_mid, prio_greatest, prio_mid, prio_mid};
   for (int q = 0; q < kSide && side_ok; ++q)
     side_ok = cudaStreamCreateWithPriority(&s->aux[q], cudaStreamNonBlocking, prio[q]) == cudaSuccess &&
               cudaEventCreateWithFlags(&s->ev_join[q], cudaEventDisableTiming) == cudaSuccess;
@@ -1534,7 +1557,7 @@ int tendency_static(const agcm_grid* g, char* base, bool tables, const void* U, 
     CUDA_TRY(cudaMemcpyAsync(Mv, g->Mv.data(), g->Mv.size() * sizeof(int), cudaMemcpyHostToDevice, st));
   {
     std::vector<int> rk, rc;
-    int nk[3];
+    int nk[agcm::kRowCls];
     row_lists(g, &rk, &rc, nk);
     if (!rk.empty())
       CUDA_TRY(cudaMemcpyAsync(base + kOffRowL, rk.data(), rk.size() * sizeof(int), cudaMemcpyHostToDevice, st));
@@ -1572,7 +1595,9 @@ int tendency_static(const agcm_grid* g, char* base, bool tables, const void* U, 
     std::vector<int> rk, rc;
     row_lists(g, &rk, &rc, G.nk);  // host only: counts (the lists were copied with the tables)
     G.nrowc = (int)rc.size();
-    G.rowfill = rows_fill_device((long long)G.nk[0] + G.nk[1] + G.nk[2]);
+    long long nitems = 0;
+    for (int c = 0; c < agcm::kRowCls; ++c) nitems += G.nk[c];
+    G.rowfill = rows_fill_device(nitems);
     G.rowk = (const int*)(base + kOffRowL);
     G.rowc = (const int*)(base + kOffRowL + kItemB);
   }
@@ -1682,7 +1707,7 @@ void fill_desc(agcm_ensemble* e) {
   for (size_t m = 0; m < e->members.size(); ++m) {
     const agcm_grid* g = e->members[m]->grid;
     std::vector<int> rk, rc;
-    int nk[3];
+    int nk[agcm::kRowCls];
     row_lists(g, &rk, &rc, nk);
     for (int it : rk) {
       e->host_items.push_back((int)m);

@@ -9,6 +9,12 @@
 
 namespace agcm {
 
+// Stride classes of the row-segment stage kernel: rows whose strides Mu_j,
+// Mv_j, Mu_{j+1} all equal kRowClsM[c] (compile-time partner offsets), and
+// a last class of rows with any strides.
+constexpr int kRowCls = 5;
+constexpr int kRowClsM[kRowCls] = {1, 3, 5, 7, 0};
+
 // Per-grid tables on the device, in the arithmetic type T of the kernels.
 // Built once per (grid, precision) by the host from the FP64 geometry.
 template <class T>
@@ -56,12 +62,12 @@ struct Geom {
   T rady;           // 1 / (a dth)
   T adl;            // a dlam
   // work items of the row-segment stage kernel (agcm_row.cuh), j << 8 | segment:
-  // nk[0] items of rows whose strides are all 1, then nk[1] items of rows
-  // whose strides are all 3, then nk[2] items of the other rows; and the
+  // nk[c] items of the rows of stride class c, listed by class: strides all
+  // kRowClsM[c] (1, 3, 5, 7), then (c = kRowCls - 1) the other rows; and the
   // nrowc rows left to the column kernel (agcm_fused.cuh)
   const int* rowk;
   const int* rowc;
-  int nk[3], nrowc;
+  int nk[kRowCls], nrowc;
   int rowfill;      // 1: the row-segment items fill the GPU at least four times over
 };
 

@@ -43,7 +43,7 @@ BYTES_PER_POINT_STEP = {4: 96, 8: 192}  # 24 words: stages read/write 6 + 9 + 9 
 NCU_TRAFFIC = {
     # kernel bracket name: (sha1 of the stage-kernel sources at capture time,
     # DRAM bytes per stage summed over the stage's launches)
-    "k_fused_stage": ("258877acbd97fc4c24f8aec545ab8875feb7f696", 957500000),
+    "k_fused_stage": ("bdf6da56225021001f2b3994ea157acdfa68fd16", 943000000),
 }
 
 # Instruction counters of the dominant kernel (ncu per-opcode counts, this
@@ -52,14 +52,14 @@ NCU_TRAFFIC = {
 # point and stage (fadd + fmul + 2 ffma), thread instructions per point, warp
 # instructions issued per point.
 NCU_OPS = {
-    "k_fused_stage": ("258877acbd97fc4c24f8aec545ab8875feb7f696", 181.0, 317.1, 9.91),
+    "k_fused_stage": ("bdf6da56225021001f2b3994ea157acdfa68fd16", 181.1, 312.6, 9.77),
 }
 
 
 # DRAM traffic of one FP32 adjoint step at 720x360x30 (all its launches: the
 # forward recompute of the two stage states and three adjoint products), from
 # an ncu capture, valid while the kernel sources are the captured ones.
-NCU_ADJ = ("ab5683aeb51634444b2503a8e5f5960cf3e1749a", 2741443584)
+NCU_ADJ = ("f69af5c5506a1652024ccb2750b972e976a7678a", 2752465920)
 
 
 def kernel_source_hash(names=("agcm_row.cuh", "agcm_fused.cuh", "agcm_common.cuh")):

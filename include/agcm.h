@@ -22,11 +22,13 @@
  *  - Element type: double for AGCM_FP64 states, float for AGCM_FP32 states.
  *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = default
  *    stream).  Calls that take a stream are asynchronous on it unless stated.
- *    A state also owns one internal stream: each stage of agcm_step,
- *    agcm_step_split, agcm_tendency and agcm_step_adjoint forks part of its
- *    rows onto it after the work already queued on `stream` and joins it back
- *    before `stream` continues, so ordering on `stream` (and capture of
- *    `stream` into a CUDA graph) is as for one launch.
+ *    A state also owns five internal streams, created with stream
+ *    priorities (the launches with the longest blocks highest): each stage
+ *    of agcm_step, agcm_step_split, agcm_tendency and agcm_step_adjoint forks
+ *    some of its launches onto them after the work already queued on
+ *    `stream` and joins them back before `stream` continues, so ordering on
+ *    `stream` (and capture of `stream` into a CUDA graph) is as for one
+ *    launch.
  *  - Errors: every call returns AGCM_OK (0) or a negative-free positive code
  *    below; agcm_last_error() returns a message for the calling thread.  The
  *    library never aborts the process and never traps on the device.

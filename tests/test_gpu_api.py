@@ -103,10 +103,10 @@ def test_profiler_counts_launches():
 
 
 def _row_kernel_launches(lu, lv, I):
-    """Launches of one stage on the row-segment path: one per stride class
-    present (rows whose strides Mu_j, Mv_j, Mu_{j+1} are all 1, all 3, other
-    rows with a halo of at most 64 columns) and one for the rows left to the
-    column kernel."""
+    """Launches of one stage of a step on the row-segment path: one per
+    stride class present (rows whose strides Mu_j, Mv_j, Mu_{j+1} are all 1,
+    all 3, all 5, all 7, other rows with a halo of at most 64 columns) and
+    one for the rows left to the column kernel."""
     J = len(lu)
     classes, col = set(), False
     for j in range(J):
@@ -115,7 +115,7 @@ def _row_kernel_launches(lu, lv, I):
         H = (max(Mu, Mv if hv else 1, M1 if hv else 1) + 4) & ~3
         if I % 4 or ((256 - 2 * H) & ~3) < 128:
             col = True
-        elif hv and Mu == Mv == M1 and Mu in (1, 3):
+        elif hv and Mu == Mv == M1 and Mu in (1, 3, 5, 7):
             classes.add(Mu)
         else:
             classes.add(0)
